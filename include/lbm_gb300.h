@@ -1,0 +1,184 @@
+/*
+ * lbm_gb300.h -- C ABI of the GB300 (sm_103a) coupled D3Q19 lattice
+ * Boltzmann library.
+ *
+ * The library computes the coupled time step of Rettinger & Ruede,
+ * "A comparative study of fluid-particle coupling methods for fully resolved
+ * lattice Boltzmann simulations" (arXiv:1702.04910): a D3Q19 lattice
+ * Boltzmann sweep (Sec. 2.1, Eq. (1)-(11)) fused with one of two fluid-
+ * particle couplings:
+ *   - PSM, partially saturated cells (Sec. 2.3, Eq. (20)-(29), Algorithm 2),
+ *     variants M1B1, M2B2, M3B2;
+ *   - MEM, momentum exchange (Sec. 2.2, Eq. (12)-(19), Algorithm 1),
+ *     boundary schemes BB and CLI (MR is reported as unsupported);
+ * followed by the per-particle force/torque reduction and an explicit
+ * rigid-body update of spherical particles.
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice units: dx = dt = 1.  Cell (x,y,z) has its centre at
+ *     (x+1/2, y+1/2, z+1/2); the domain is [0,nx) x [0,ny) x [0,nz),
+ *     periodic in x and y, periodic or closed (resting no-slip walls at
+ *     z = 0 and z = nz) in z.
+ *   - PDF fields are structure-of-arrays, index q*N + x + nx*(y + ny*z) with
+ *     N = nx*ny*nz and q in the order: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z;
+ *     7..18 = (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),(-1,0,-1),
+ *     (+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1).
+ *   - The handle owns all device memory it allocates.  Every buffer passed in
+ *     is owned by the caller and only read or written during the call (or,
+ *     for device pointers, in stream order on the handle's stream).
+ *   - Work is enqueued on the CUDA stream given to lbm_create (the legacy
+ *     default stream if NULL).  Calls that return data to host memory
+ *     synchronise that stream.
+ *   - No C++ exception crosses this interface.  Every call returns an
+ *     lbm_status; on failure lbm_last_error() describes the cause.  Device
+ *     kernels never trap: they raise a status word that the next
+ *     synchronising call (lbm_get_forces, lbm_get_particles, lbm_get_fields,
+ *     lbm_synchronize) reports.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,         /* invalid argument; nothing was changed            */
+    LBM_ERR_CUDA = -2,        /* a CUDA runtime call failed                       */
+    LBM_ERR_OOM = -3,         /* device or pinned host allocation failed          */
+    LBM_ERR_UNSTABLE = -4,    /* reserved: non-finite state detected              */
+    LBM_ERR_DOMAIN = -5,      /* a particle left the domain through a closed wall */
+    LBM_ERR_TIMEOUT = -6,     /* reserved: a bounded device wait gave up          */
+    LBM_ERR_UNSUPPORTED = -7  /* configuration not implemented (e.g. MEM MR)      */
+} lbm_status;
+
+/* Coupling of Sec. 2.2 / 2.3.  LBM_NONE runs the plain fluid sweep. */
+typedef enum {
+    LBM_PSM_M1B1 = 0, /* Eq. (21) with Eq. (23)                      */
+    LBM_PSM_M2B2 = 1, /* Eq. (22) with Eq. (24)                      */
+    LBM_PSM_M3B2 = 2, /* Eq. (22) with Eq. (25)                      */
+    LBM_MEM_BB = 3,   /* Eq. (12)                                    */
+    LBM_MEM_CLI = 4,  /* Eq. (14)                                    */
+    LBM_MEM_MR = 5,   /* Eq. (15): coefficients not given; unsupported */
+    LBM_NONE = 6
+} lbm_coupling;
+
+/* Fluid collision operator: BGK Eq. (5) or TRT Eq. (9)-(11). */
+typedef enum { LBM_BGK = 0, LBM_TRT = 1 } lbm_collision;
+
+/* PDF storage and collision arithmetic.  Forces, solid fractions and the
+ * rigid-body update are FP64 in every mode. */
+typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1 } lbm_storage;
+
+typedef struct {
+    int nx, ny, nz;            /* cells per axis, each >= 1                        */
+    int bc_z;                  /* 0: periodic in z; 1: resting no-slip walls      */
+    int collision;             /* lbm_collision                                   */
+    int coupling;              /* lbm_coupling                                    */
+    double tau;                /* relaxation time, > 1/2 (nu = (tau - 1/2)/3)     */
+    double magic;              /* TRT Lambda of Eq. (11), e.g. 3/16               */
+    double force_density[3];   /* f_ext of Eq. (7), acts on the fluid             */
+    double gravity[3];         /* acceleration acting on the particles            */
+    double rho0;               /* reference density rho_0 (> 0)                   */
+    int subsample;             /* PSM: n of the n^3 supersampling (0 -> 4)        */
+    int lbm_subcycles;         /* LBM sweeps per global step (0 -> 2 MEM, 1 PSM)  */
+    int wall_contact;          /* 1: keep spheres one cell off closed z walls     */
+    int storage;               /* lbm_storage                                     */
+} lbm_config;
+
+/* Rigid spherical particle (Eq. (13) velocity field). */
+typedef struct {
+    double x[3];       /* centre X_p                                 */
+    double u[3];       /* translational velocity U_p                 */
+    double omega[3];   /* angular velocity Omega_p                   */
+    double diameter;   /* D                                          */
+    double density;    /* rho_p                                      */
+    int fixed;         /* 1: position and velocity are held constant */
+} lbm_particle;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Field selectors of lbm_get_fields / lbm_set_fields. */
+enum {
+    LBM_FIELD_PDF = 0,     /* stored post-collision PDFs (state), 19*N of the storage type */
+    LBM_FIELD_PDF_PRE = 1, /* set only: pre-collision PDFs f at t = 0, 19*N doubles        */
+    LBM_FIELD_RHO = 2,     /* get only: fluid density rho_f, N doubles                     */
+    LBM_FIELD_U = 3,       /* get only: velocity u, Eq. (8) / (27), 3*N doubles [cell][3]   */
+    LBM_FIELD_EPS = 4,     /* get only: PSM solid fraction sum_s eps_s, N doubles          */
+    LBM_FIELD_FLAG = 5     /* get only: MEM owner (0 fluid, s+1 inside particle s), N int32 */
+};
+
+/* Create a simulation.  Validates *cfg (LBM_ERR_ARG on a bad value,
+ * LBM_ERR_UNSUPPORTED for LBM_MEM_MR), allocates two PDF buffers of
+ * 19*N elements on the current CUDA device and initialises the fluid at rest
+ * (f = f_eq(rho0, 0), Eq. (3)).  stream: a cudaStream_t or NULL.
+ * On success *out receives the handle; release it with lbm_destroy. */
+lbm_status lbm_create(const lbm_config *cfg, void *stream, lbm_handle **out);
+
+/* Replace the particle state with n host records (n <= 32; D >= 1 and D + 4
+ * cells below each periodic extent).  Before the first step this defines the
+ * initial mapping (MEM, Sec. 2.2) and the solid fractions (PSM, Sec. 2.3).
+ * Between steps with MEM coupling, cells uncovered by the replacement are
+ * refilled with f_eq(rho0, v) (the particle count must not change then). */
+lbm_status lbm_set_particles(lbm_handle *h, int n, const lbm_particle *host_in);
+
+/* Copy the current particle state into host_out (n records). Synchronises. */
+lbm_status lbm_get_particles(lbm_handle *h, lbm_particle *host_out);
+
+/* Set the pre-collision state at t = 0 to f_eq(rho, u) in every cell, Eq. (3). */
+lbm_status lbm_init_equilibrium(lbm_handle *h, double rho, const double u[3]);
+
+/* Advance nsteps global time steps (Algorithm 1 for MEM, Algorithm 2 for
+ * PSM; MEM runs lbm_subcycles LBM sweeps per step).  Asynchronous: returns
+ * after enqueueing. */
+lbm_status lbm_step(lbm_handle *h, int nsteps);
+
+/* Hydrodynamic force and torque of the last global step, Eq. (17)-(18)
+ * (MEM, averaged over the subcycles) or Eq. (28)-(29) (PSM).  F and T are
+ * host arrays of 3*n doubles [particle][3].  Synchronises and reports any
+ * device status raised since the last synchronising call. */
+lbm_status lbm_get_forces(lbm_handle *h, double *F, double *T);
+
+/* Copy a field (see LBM_FIELD_*) into dst, a host or device buffer of
+ * exactly `bytes` bytes (LBM_ERR_ARG otherwise).  RHO/U/EPS/FLAG describe
+ * the pre-collision state at the start of the next step.  Synchronises. */
+lbm_status lbm_get_fields(lbm_handle *h, int what, void *dst, size_t bytes, int dst_is_device);
+
+/* Overwrite a field from src (host or device, exactly `bytes` bytes).
+ * LBM_FIELD_PDF restores a state saved with lbm_get_fields (checkpoint);
+ * LBM_FIELD_PDF_PRE sets the pre-collision PDFs at t = 0. */
+lbm_status lbm_set_fields(lbm_handle *h, int what, const void *src, size_t bytes, int src_is_device);
+
+/* Wait for all enqueued work and report device status. */
+lbm_status lbm_synchronize(lbm_handle *h);
+
+/* Per-kernel device timing with CUDA events on the handle's stream.
+ * lbm_profile_enable(h, 1) starts recording (and clears the totals);
+ * lbm_profile_read returns, for each kernel class k < n_classes
+ * (0 bulk sweep, 1 near-particle sweep, 2 force reduction, 3 rigid-body
+ * update, 4 MEM refill, 5 other), the summed milliseconds and launches.
+ * Reading synchronises the stream. */
+lbm_status lbm_profile_enable(lbm_handle *h, int enable);
+lbm_status lbm_profile_read(lbm_handle *h, int n_classes, double *ms, long long *launches);
+
+/* Bytes of device memory held by the handle. */
+size_t lbm_device_bytes(const lbm_handle *h);
+
+/* Release every resource of the handle (NULL is ignored). */
+void lbm_destroy(lbm_handle *h);
+
+/* Human-readable description of the last failure on h ("" if none; a
+ * static string for h == NULL). */
+const char *lbm_last_error(const lbm_handle *h);
+
+/* ABI version of this header: 1. */
+int lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of ``liblbm_gb300.so`` (C ABI in ``include/lbm_gb300.h``).
+
+Argument marshalling only: every step of the coupled lattice Boltzmann path
+runs in the CUDA library.  There is no fallback: if the library is missing or
+cannot be loaded, :func:`load` raises.
+
+The module-level functions carry the C names (``lbm_create``, ``lbm_step``,
+...).  :class:`Simulation` bundles a handle with NumPy / torch-friendly
+marshalling for the tests and the benchmark.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+NQ = 19
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM = 0, -1, -2, -3
+LBM_ERR_UNSTABLE, LBM_ERR_DOMAIN, LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED = -4, -5, -6, -7
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
+                -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_DOMAIN", -6: "LBM_ERR_TIMEOUT",
+                -7: "LBM_ERR_UNSUPPORTED"}
+
+COUPLING = {"PSM_M1B1": 0, "PSM_M2B2": 1, "PSM_M3B2": 2, "MEM_BB": 3, "MEM_CLI": 4,
+            "MEM_MR": 5, "NONE": 6}
+COLLISION = {"BGK": 0, "TRT": 1}
+STORAGE = {"f64": 0, "f32": 1}
+FIELD_PDF, FIELD_PDF_PRE, FIELD_RHO, FIELD_U, FIELD_EPS, FIELD_FLAG = range(6)
+PROFILE_CLASSES = ("bulk", "near", "force_total", "rigid_body", "refill", "other")
+
+EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_equilibrium",
+            "lbm_step", "lbm_get_forces", "lbm_get_fields", "lbm_set_fields",
+            "lbm_synchronize", "lbm_profile_enable", "lbm_profile_read", "lbm_device_bytes",
+            "lbm_destroy", "lbm_last_error", "lbm_abi_version")
+
+
+class LbmConfig(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("bc_z", ct.c_int),
+                ("collision", ct.c_int), ("coupling", ct.c_int), ("tau", ct.c_double),
+                ("magic", ct.c_double), ("force_density", ct.c_double * 3),
+                ("gravity", ct.c_double * 3), ("rho0", ct.c_double), ("subsample", ct.c_int),
+                ("lbm_subcycles", ct.c_int), ("wall_contact", ct.c_int), ("storage", ct.c_int)]
+
+
+class LbmParticle(ct.Structure):
+    _fields_ = [("x", ct.c_double * 3), ("u", ct.c_double * 3), ("omega", ct.c_double * 3),
+                ("diameter", ct.c_double), ("density", ct.c_double), ("fixed", ct.c_int)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if allowed and missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library {path} is not built")
+            _build.build()
+        lib = ct.CDLL(path)
+        vp, dp, i, sz = ct.c_void_p, ct.POINTER(ct.c_double), ct.c_int, ct.c_size_t
+        sig = {
+            "lbm_create": (i, [ct.POINTER(LbmConfig), vp, ct.POINTER(vp)]),
+            "lbm_set_particles": (i, [vp, i, ct.POINTER(LbmParticle)]),
+            "lbm_get_particles": (i, [vp, ct.POINTER(LbmParticle)]),
+            "lbm_init_equilibrium": (i, [vp, ct.c_double, dp]),
+            "lbm_step": (i, [vp, i]),
+            "lbm_get_forces": (i, [vp, dp, dp]),
+            "lbm_get_fields": (i, [vp, i, vp, sz, i]),
+            "lbm_set_fields": (i, [vp, i, vp, sz, i]),
+            "lbm_synchronize": (i, [vp]),
+            "lbm_profile_enable": (i, [vp, i]),
+            "lbm_profile_read": (i, [vp, i, dp, ct.POINTER(ct.c_longlong)]),
+            "lbm_device_bytes": (sz, [vp]),
+            "lbm_destroy": (None, [vp]),
+            "lbm_last_error": (ct.c_char_p, [vp]),
+            "lbm_abi_version": (i, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ---- C-named entry points (marshalling only) -------------------------------------
+def _check(h, st):
+    if st != LBM_OK:
+        msg = load().lbm_last_error(h)
+        raise LbmError(st, msg.decode() if msg else "")
+    return st
+
+
+def make_config(shape, *, coupling="NONE", collision="TRT", tau=0.8, magic=3.0 / 16.0,
+                fext=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0), rho0=1.0, bc_z=0, subsample=4,
+                subcycles=0, wall_contact=0, storage="f64") -> LbmConfig:
+    c = LbmConfig()
+    c.nx, c.ny, c.nz = (int(v) for v in shape)
+    c.bc_z = int(bc_z)
+    c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+    c.coupling = COUPLING[coupling] if isinstance(coupling, str) else int(coupling)
+    c.tau, c.magic = float(tau), float(magic)
+    for a in range(3):
+        c.force_density[a] = float(fext[a])
+        c.gravity[a] = float(gravity[a])
+    c.rho0 = float(rho0)
+    c.subsample, c.lbm_subcycles, c.wall_contact = int(subsample), int(subcycles), int(wall_contact)
+    c.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    return c
+
+
+def particles_to_c(particles):
+    arr = (LbmParticle * max(1, len(particles)))()
+    for i, d in enumerate(particles):
+        for a in range(3):
+            arr[i].x[a] = float(d["x"][a])
+            arr[i].u[a] = float(d.get("u", (0, 0, 0))[a])
+            arr[i].omega[a] = float(d.get("omega", (0, 0, 0))[a])
+        arr[i].diameter = float(d["diameter"])
+        arr[i].density = float(d.get("density", 1.0))
+        arr[i].fixed = int(d.get("fixed", 0))
+    return arr
+
+
+def lbm_create(cfg: LbmConfig, stream: int | None = None) -> ct.c_void_p:
+    lib = load()
+    h = ct.c_void_p()
+    st = lib.lbm_create(ct.byref(cfg), ct.c_void_p(stream or 0), ct.byref(h))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_create rejected the configuration")
+    return h
+
+
+def lbm_destroy(h) -> None:
+    load().lbm_destroy(h)
+
+
+def lbm_set_particles(h, particles) -> None:
+    _check(h, load().lbm_set_particles(h, len(particles), particles_to_c(particles)))
+
+
+def lbm_get_particles(h, n: int):
+    arr = (LbmParticle * max(1, n))()
+    _check(h, load().lbm_get_particles(h, arr))
+    return [{"x": np.array(arr[i].x[:]), "u": np.array(arr[i].u[:]),
+             "omega": np.array(arr[i].omega[:]), "diameter": arr[i].diameter,
+             "density": arr[i].density, "fixed": arr[i].fixed} for i in range(n)]
+
+
+def lbm_init_equilibrium(h, rho: float, u) -> None:
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    _check(h, load().lbm_init_equilibrium(h, float(rho), uu.ctypes.data_as(ct.POINTER(ct.c_double))))
+
+
+def lbm_step(h, nsteps: int) -> None:
+    _check(h, load().lbm_step(h, int(nsteps)))
+
+
+def lbm_get_forces(h, n: int, F: np.ndarray | None = None, T: np.ndarray | None = None):
+    F = np.zeros((max(n, 1), 3)) if F is None else F
+    T = np.zeros((max(n, 1), 3)) if T is None else T
+    _check(h, load().lbm_get_forces(h, F.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                    T.ctypes.data_as(ct.POINTER(ct.c_double))))
+    return F[:n], T[:n]
+
+
+def lbm_get_fields(h, what: int, ptr: int, nbytes: int, is_device: bool) -> None:
+    _check(h, load().lbm_get_fields(h, int(what), ct.c_void_p(ptr), nbytes, int(is_device)))
+
+
+def lbm_set_fields(h, what: int, ptr: int, nbytes: int, is_device: bool) -> None:
+    _check(h, load().lbm_set_fields(h, int(what), ct.c_void_p(ptr), nbytes, int(is_device)))
+
+
+def lbm_synchronize(h) -> None:
+    _check(h, load().lbm_synchronize(h))
+
+
+def lbm_profile_enable(h, enable: bool) -> None:
+    _check(h, load().lbm_profile_enable(h, int(bool(enable))))
+
+
+def lbm_profile_read(h):
+    n = len(PROFILE_CLASSES)
+    ms = (ct.c_double * n)()
+    cnt = (ct.c_longlong * n)()
+    _check(h, load().lbm_profile_read(h, n, ms, cnt))
+    return {PROFILE_CLASSES[k]: (ms[k], cnt[k]) for k in range(n)}
+
+
+def lbm_device_bytes(h) -> int:
+    return int(load().lbm_device_bytes(h))
+
+
+# ---- convenience wrapper ------------------------------------------------------------
+class Simulation:
+    """One library handle; arrays are NumPy (host) unless noted."""
+
+    def __init__(self, shape, stream: int | None = None, **kw):
+        self.shape = tuple(int(v) for v in shape)
+        self.storage = kw.get("storage", "f64")
+        self.cfg = make_config(shape, **kw)
+        self.h = lbm_create(self.cfg, stream)
+        self.np = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ncells(self):
+        nx, ny, nz = self.shape
+        return nx * ny * nz
+
+    @property
+    def pdf_dtype(self):
+        return np.float64 if self.storage == "f64" else np.float32
+
+    def set_particles(self, particles):
+        lbm_set_particles(self.h, particles)
+        self.np = len(particles)
+
+    def get_particles(self):
+        return lbm_get_particles(self.h, self.np)
+
+    def init_equilibrium(self, rho=1.0, u=(0.0, 0.0, 0.0)):
+        lbm_init_equilibrium(self.h, rho, u)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def forces(self):
+        return lbm_get_forces(self.h, self.np)
+
+    def set_pdf_pre(self, f: np.ndarray):
+        a = np.ascontiguousarray(f, dtype=np.float64)
+        assert a.size == NQ * self.ncells
+        lbm_set_fields(self.h, FIELD_PDF_PRE, a.ctypes.data, a.nbytes, False)
+
+    def pdf(self) -> np.ndarray:
+        nx, ny, nz = self.shape
+        out = np.empty((NQ, nz, ny, nx), dtype=self.pdf_dtype)
+        lbm_get_fields(self.h, FIELD_PDF, out.ctypes.data, out.nbytes, False)
+        return out
+
+    def set_pdf(self, f: np.ndarray):
+        a = np.ascontiguousarray(f, dtype=self.pdf_dtype)
+        lbm_set_fields(self.h, FIELD_PDF, a.ctypes.data, a.nbytes, False)
+
+    def macro(self):
+        nx, ny, nz = self.shape
+        rho = np.empty((nz, ny, nx))
+        u = np.empty((nz, ny, nx, 3))
+        lbm_get_fields(self.h, FIELD_RHO, rho.ctypes.data, rho.nbytes, False)
+        lbm_get_fields(self.h, FIELD_U, u.ctypes.data, u.nbytes, False)
+        return rho, u
+
+    def eps(self):
+        nx, ny, nz = self.shape
+        out = np.empty((nz, ny, nx))
+        lbm_get_fields(self.h, FIELD_EPS, out.ctypes.data, out.nbytes, False)
+        return out
+
+    def flags(self):
+        nx, ny, nz = self.shape
+        out = np.empty((nz, ny, nx), dtype=np.int32)
+        lbm_get_fields(self.h, FIELD_FLAG, out.ctypes.data, out.nbytes, False)
+        return out
+
+    def synchronize(self):
+        lbm_synchronize(self.h)

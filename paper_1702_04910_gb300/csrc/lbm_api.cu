@@ -1,0 +1,641 @@
+// C ABI of the coupled D3Q19 library (declarations and contracts in
+// include/lbm_gb300.h).  Host orchestration of one global step:
+//
+//   PSM (Algorithm 2 of Rettinger & Ruede, arXiv:1702.04910):
+//     bulk + near sweep (solid fractions, weighted collision, force partials)
+//     -> force total -> rigid-body update (dt = 1)
+//   MEM (Algorithm 1):
+//     lbm_subcycles x (bulk + near sweep with link boundary conditions and
+//     link-force partials) -> averaged force total -> rigid-body update
+//     (dt = number of subcycles) -> re-mapping with PDF reconstruction
+//
+// Everything is enqueued on the handle's stream; nothing here synchronises
+// except the calls that return data to the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm_gb300.h"
+#include "lbm_launch.h"
+
+using namespace lbmgpu;
+
+namespace {
+
+constexpr int N_PROFILE_CLASSES = 6;
+enum { PC_BULK = 0, PC_NEAR = 1, PC_FINAL = 2, PC_RIGID = 3, PC_REFILL = 4, PC_OTHER = 5 };
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int cls;
+};
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_config cfg;
+    cudaStream_t stream;
+    int device;
+    Geom g;
+    int storage;       // 0 FP64, 1 FP32
+    size_t esize;      // bytes per stored PDF value
+    void* buf[2];
+    int cur;           // buffer holding the stored state
+    int pending_pre;   // buf[cur] holds pre-collision PDFs (first sweep does not stream)
+    int kind;          // 0 none, 1 PSM, 2 MEM
+    int variant;
+    int subcycles;
+    int np;
+    int have_particles;
+    double maxd;
+    DevParticle* d_parts;
+    DevParticle* d_prev;
+    DevParticle* d_tmp;
+    double* d_force;     // [np][6]
+    double* d_partials;  // [subcycles][np][ntiles][6]
+    int* d_status;
+    double* h_stage;     // pinned: status word + np*6 forces
+    size_t dev_bytes;
+    Coll<double> kd;
+    Coll<float> kf;
+    // profiling
+    int profiling;
+    std::vector<EventPair> events;
+    std::vector<cudaEvent_t> pool;
+    char err[512];
+};
+
+namespace {
+
+lbm_status fail(lbm_handle* h, lbm_status st, const char* msg) {
+    if (h) std::snprintf(h->err, sizeof(h->err), "%s", msg);
+    return st;
+}
+
+lbm_status cuda_fail(lbm_handle* h, cudaError_t e, const char* where) {
+    if (h)
+        std::snprintf(h->err, sizeof(h->err), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+#define CK(h, call, where)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+    } while (0)
+
+bool is_psm(int c) { return c == LBM_PSM_M1B1 || c == LBM_PSM_M2B2 || c == LBM_PSM_M3B2; }
+bool is_mem(int c) { return c == LBM_MEM_BB || c == LBM_MEM_CLI || c == LBM_MEM_MR; }
+
+cudaEvent_t take_event(lbm_handle* h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records an event before a launch when profiling; returns the pair index.
+int prof_begin(lbm_handle* h, int cls) {
+    if (!h->profiling) return -1;
+    EventPair p{take_event(h), take_event(h), cls};
+    if (!p.a || !p.b) return -1;
+    cudaEventRecord(p.a, h->stream);
+    h->events.push_back(p);
+    return (int)h->events.size() - 1;
+}
+void prof_end(lbm_handle* h, int i) {
+    if (i >= 0) cudaEventRecord(h->events[i].b, h->stream);
+}
+
+Launch base_launch(lbm_handle* h) {
+    Launch L{};
+    L.g = h->g;
+    L.kd = h->kd;
+    L.kf = h->kf;
+    L.cp.kind = h->kind;
+    L.cp.variant = h->variant;
+    L.cp.np = h->np;
+    L.cp.subsample = h->cfg.subsample;
+    L.cp.tau = h->cfg.tau;
+    L.cp.rho0 = h->cfg.rho0;
+    L.parts = h->d_parts;
+    L.parts_prev = h->d_prev;
+    L.partials = h->d_partials;
+    L.status = h->d_status;
+    L.nostream = 0;
+    L.all_tiles = 0;
+    L.block = dim3(h->g.tx, h->g.ty, 1);
+    L.stream = h->stream;
+    // near-kernel tile box: tiles spanned by D + 2 halo + 1 cells, plus slack
+    // for a misaligned start and a ragged last tile
+    const double span = h->maxd + 2.0 * NEAR_HALO + 1.0;
+    const int T[3] = {h->g.tx, h->g.ty, 1};
+    const int nt[3] = {h->g.ntx, h->g.nty, h->g.ntz};
+    for (int a = 0; a < 3; ++a) {
+        int b = (int)std::ceil(span / T[a]) + 2;
+        L.box[a] = std::min(b, nt[a]);
+    }
+    return L;
+}
+
+// Collision constants (computed in FP64, rounded once to C).
+template <typename C>
+Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) {
+    Coll<C> k{};
+    k.lam_p = (C)lp;
+    k.lam_m = (C)lm;
+    k.rho0 = (C)rho0;
+    k.inv_rho0 = (C)(1.0 / rho0);
+    k.fx = (C)fe[0];
+    k.fy = (C)fe[1];
+    k.fz = (C)fe[2];
+    k.has_force = (fe[0] != 0.0 || fe[1] != 0.0 || fe[2] != 0.0);
+    k.alpha = (C)(1.0 + 0.5 * (lp + lm));
+    k.beta = (C)(0.5 * (lp - lm));
+    k.c0 = (C)(1.0 + lp);
+    k.m15r0 = (C)(-1.5 * rho0);
+    const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    for (int c = 0; c < 3; ++c) {
+        k.lpw[c] = (C)(lp * w[c]);
+        k.k1w[c] = (C)(4.5 * lp * w[c] * rho0);
+        k.k2w[c] = (C)(3.0 * lm * w[c] * rho0);
+        k.hw[c] = (C)(3.0 * w[c]);
+    }
+    for (int q = 1; q < NQ; q += 2) {
+        const double cf = cx(q) * fe[0] + cy(q) * fe[1] + cz(q) * fe[2];
+        k.gq[(q - 1) / 2] = (C)(9.0 * wq(q) * cf);
+        k.fq[(q - 1) / 2] = (C)(3.0 * wq(q) * cf);
+    }
+    return k;
+}
+
+long long ntiles(const lbm_handle* h) { return (long long)h->g.ntx * h->g.nty * h->g.ntz; }
+
+lbm_status free_particles(lbm_handle* h) {
+    cudaFree(h->d_parts);
+    cudaFree(h->d_prev);
+    cudaFree(h->d_tmp);
+    cudaFree(h->d_force);
+    cudaFree(h->d_partials);
+    h->d_parts = h->d_prev = h->d_tmp = nullptr;
+    h->d_force = h->d_partials = nullptr;
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    h->h_stage = nullptr;
+    return LBM_OK;
+}
+
+lbm_status alloc_particles(lbm_handle* h, int n) {
+    free_particles(h);
+    size_t np = (size_t)std::max(n, 1);
+    size_t part_bytes = sizeof(DevParticle) * np;
+    size_t partial_bytes = sizeof(double) * 6 * (size_t)h->subcycles * np * (size_t)ntiles(h);
+    CK(h, cudaMalloc(&h->d_parts, part_bytes), "cudaMalloc particles");
+    CK(h, cudaMalloc(&h->d_prev, part_bytes), "cudaMalloc particles");
+    CK(h, cudaMalloc(&h->d_tmp, part_bytes), "cudaMalloc particles");
+    CK(h, cudaMalloc(&h->d_force, sizeof(double) * 6 * np), "cudaMalloc forces");
+    CK(h, cudaMalloc(&h->d_partials, partial_bytes), "cudaMalloc force partials");
+    CK(h, cudaMemsetAsync(h->d_force, 0, sizeof(double) * 6 * np, h->stream), "memset");
+    CK(h, cudaMemsetAsync(h->d_partials, 0, partial_bytes, h->stream), "memset");
+    CK(h, cudaMallocHost(&h->h_stage, sizeof(double) * (6 * np + 1)), "cudaMallocHost");
+    h->dev_bytes += 3 * part_bytes + sizeof(double) * 6 * np + partial_bytes;
+    return LBM_OK;
+}
+
+// MEM: collide every cell of the stored pre-collision field (no stream).
+lbm_status collide_in_place(lbm_handle* h) {
+    Launch L = base_launch(h);
+    L.nostream = 1;
+    L.all_tiles = 1;
+    int pi = prof_begin(h, PC_OTHER);
+    CK(h, launch_bulk(h->storage, h->buf[h->cur], h->buf[1 - h->cur], L), "collide launch");
+    prof_end(h, pi);
+    h->cur = 1 - h->cur;
+    h->pending_pre = 0;
+    return LBM_OK;
+}
+
+// The stored buffer now holds pre-collision PDFs of t = 0.
+lbm_status after_pre_state(lbm_handle* h) {
+    if (h->kind == 2) return collide_in_place(h);
+    h->pending_pre = 1;
+    return LBM_OK;
+}
+
+lbm_status sweep(lbm_handle* h, int sub) {
+    Launch L = base_launch(h);
+    L.nostream = h->pending_pre;
+    L.partials = h->d_partials + (size_t)sub * (size_t)std::max(h->np, 1) * ntiles(h) * 6;
+    const void* src = h->buf[h->cur];
+    void* dst = h->buf[1 - h->cur];
+    int pi = prof_begin(h, PC_BULK);
+    CK(h, launch_bulk(h->storage, src, dst, L), "bulk sweep launch");
+    prof_end(h, pi);
+    if (h->np > 0) {
+        pi = prof_begin(h, PC_NEAR);
+        CK(h, launch_near(h->storage, src, dst, L), "near sweep launch");
+        prof_end(h, pi);
+    }
+    h->cur = 1 - h->cur;
+    h->pending_pre = 0;
+    return LBM_OK;
+}
+
+lbm_status step_once(lbm_handle* h) {
+    lbm_status st;
+    const int coupled = h->np > 0 && h->kind != 0;
+    const int nsub = h->kind == 2 ? h->subcycles : 1;
+    for (int s = 0; s < nsub; ++s)
+        if ((st = sweep(h, s)) != LBM_OK) return st;
+    if (!coupled) return LBM_OK;
+    Launch L = base_launch(h);
+    int pi = prof_begin(h, PC_FINAL);
+    CK(h, launch_finalize(L, nsub, h->d_force), "force total launch");
+    prof_end(h, pi);
+    pi = prof_begin(h, PC_RIGID);
+    CK(h, launch_rigid_body(L, h->d_force, h->cfg.gravity[0], h->cfg.gravity[1],
+                            h->cfg.gravity[2], (double)nsub, h->cfg.wall_contact),
+       "rigid body launch");
+    prof_end(h, pi);
+    if (h->kind == 2) {
+        // re-map with the new state; rebuild uncovered cells (src of the last sweep)
+        L.box[0] = (int)std::ceil(h->maxd) + 4;
+        pi = prof_begin(h, PC_REFILL);
+        CK(h, launch_refill(h->storage, h->buf[1 - h->cur], h->buf[h->cur], L, h->d_prev,
+                            h->d_parts, 1),
+           "refill launch");
+        prof_end(h, pi);
+    }
+    return LBM_OK;
+}
+
+lbm_status read_status(lbm_handle* h) {
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&h->h_stage[0], h->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                          h->stream),
+       "status copy");
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    std::memcpy(&st, &h->h_stage[0], sizeof(int));
+    if (st) {
+        CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream), "status reset");
+        if (st & ST_DOMAIN) return fail(h, LBM_ERR_DOMAIN, "a particle left the domain through a closed wall");
+        if (st & ST_TOO_MANY_OBJECTS)
+            return fail(h, LBM_ERR_UNSUPPORTED, "more than two particles touch one cell");
+        return fail(h, LBM_ERR_CUDA, "device status raised");
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_abi_version(void) { return 1; }
+
+const char* lbm_last_error(const lbm_handle* h) {
+    return h ? h->err : "no handle";
+}
+
+size_t lbm_device_bytes(const lbm_handle* h) { return h ? h->dev_bytes : 0; }
+
+lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
+    if (!cfg || !out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return LBM_ERR_ARG;
+    if (!(cfg->tau > 0.5) || !(cfg->rho0 > 0.0) || !std::isfinite(cfg->tau)) return LBM_ERR_ARG;
+    if (cfg->coupling < 0 || cfg->coupling > LBM_NONE) return LBM_ERR_ARG;
+    if (cfg->collision != LBM_BGK && cfg->collision != LBM_TRT) return LBM_ERR_ARG;
+    if (cfg->storage != LBM_STORE_F64 && cfg->storage != LBM_STORE_F32) return LBM_ERR_ARG;
+    if (cfg->bc_z != 0 && cfg->bc_z != 1) return LBM_ERR_ARG;
+    if (cfg->subsample < 0 || cfg->subsample > 64 || cfg->lbm_subcycles < 0) return LBM_ERR_ARG;
+    if (cfg->coupling == LBM_MEM_MR) return LBM_ERR_UNSUPPORTED;
+    if (cfg->collision == LBM_TRT) {
+        double lp = -1.0 / cfg->tau;
+        double denom = cfg->magic / (0.5 + 1.0 / lp) - 0.5;
+        if (!(cfg->magic > 0.0) || denom == 0.0) return LBM_ERR_ARG;
+        double lm = 1.0 / denom;
+        if (!(lm > -2.0 && lm < 0.0)) return LBM_ERR_ARG;
+    }
+    const long long n = (long long)cfg->nx * cfg->ny * cfg->nz;
+    if (n > (1LL << 40)) return LBM_ERR_ARG;
+
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ERR_OOM;
+    h->cfg = *cfg;
+    if (h->cfg.subsample == 0) h->cfg.subsample = 4;
+    h->stream = (cudaStream_t)stream;
+    cudaGetDevice(&h->device);
+    h->storage = cfg->storage == LBM_STORE_F64 ? 0 : 1;
+    h->esize = h->storage == 0 ? sizeof(double) : sizeof(float);
+    h->kind = is_psm(cfg->coupling) ? 1 : (is_mem(cfg->coupling) ? 2 : 0);
+    h->variant = h->kind == 1 ? cfg->coupling - LBM_PSM_M1B1
+                              : (h->kind == 2 ? cfg->coupling - LBM_MEM_BB : 0);
+    h->subcycles = cfg->lbm_subcycles > 0 ? cfg->lbm_subcycles : (h->kind == 2 ? 2 : 1);
+    if (h->kind != 2) h->subcycles = 1;
+
+    Geom& g = h->g;
+    g.nx = cfg->nx;
+    g.ny = cfg->ny;
+    g.nz = cfg->nz;
+    g.bc_z = cfg->bc_z;
+    g.n = n;
+    g.tx = cfg->nx >= 128 ? 128 : (cfg->nx >= 64 ? 64 : 32);
+    g.ty = 256 / g.tx;
+    g.ntx = (cfg->nx + g.tx - 1) / g.tx;
+    g.nty = (cfg->ny + g.ty - 1) / g.ty;
+    g.ntz = cfg->nz;
+
+    const double lp = -1.0 / cfg->tau;
+    const double lm = cfg->collision == LBM_TRT ? 1.0 / (cfg->magic / (0.5 + 1.0 / lp) - 0.5) : lp;
+    h->kd = make_coll<double>(lp, lm, cfg->rho0, cfg->force_density);
+    h->kf = make_coll<float>(lp, lm, cfg->rho0, cfg->force_density);
+
+    size_t bytes = (size_t)NQ * (size_t)n * h->esize;
+    cudaError_t e = cudaMalloc(&h->buf[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
+    if (e != cudaSuccess) {
+        lbm_status st = cuda_fail(h, e, "cudaMalloc PDF buffers");
+        lbm_destroy(h);
+        return st;
+    }
+    h->dev_bytes = 2 * bytes + sizeof(int);
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+    lbm_status st = alloc_particles(h, 0);
+    if (st == LBM_OK) {
+        const double u0[3] = {0.0, 0.0, 0.0};
+        st = lbm_init_equilibrium(h, cfg->rho0, u0);
+    }
+    if (st != LBM_OK) {
+        lbm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->d_status);
+    free_particles(h);
+    for (auto& p : h->events) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    delete h;
+}
+
+lbm_status lbm_set_particles(lbm_handle* h, int n, const lbm_particle* host_in) {
+    if (!h) return LBM_ERR_ARG;
+    if (n < 0 || n > MAX_PARTICLES || (n > 0 && !host_in))
+        return fail(h, LBM_ERR_ARG, "particle count must be 0..32");
+    double maxd = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const lbm_particle& p = host_in[i];
+        const double D = p.diameter;
+        bool finite = std::isfinite(D) && std::isfinite(p.density);
+        for (int a = 0; a < 3; ++a)
+            finite = finite && std::isfinite(p.x[a]) && std::isfinite(p.u[a]) && std::isfinite(p.omega[a]);
+        if (!finite || !(D >= 1.0) || !(p.density > 0.0))
+            return fail(h, LBM_ERR_ARG, "particle with non-finite value, D < 1 or density <= 0");
+        const double need = D + 2.0 * NEAR_HALO + 2.0;
+        if (need > h->g.nx || need > h->g.ny || (!h->g.bc_z && need > h->g.nz))
+            return fail(h, LBM_ERR_ARG, "particle diameter + 6 exceeds a periodic extent");
+        if (h->g.bc_z && (p.x[2] - 0.5 * D < 0.0 || p.x[2] + 0.5 * D > h->g.nz))
+            return fail(h, LBM_ERR_ARG, "particle crosses a closed wall");
+        maxd = std::max(maxd, D);
+    }
+    const bool remap = h->have_particles && h->kind == 2 && n == h->np && n > 0;
+    if (h->have_particles && h->kind == 2 && n != h->np && h->np > 0)
+        return fail(h, LBM_ERR_ARG, "the particle count cannot change once MEM particles are mapped");
+    std::vector<DevParticle> recs((size_t)std::max(n, 1));
+    for (int i = 0; i < n; ++i) {
+        const lbm_particle& p = host_in[i];
+        DevParticle d{};
+        for (int a = 0; a < 3; ++a) {
+            double xa = p.x[a];
+            const int L = a == 0 ? h->g.nx : (a == 1 ? h->g.ny : h->g.nz);
+            if (!(a == 2 && h->g.bc_z)) {
+                xa = std::fmod(xa, (double)L);
+                if (xa < 0.0) xa += L;
+            }
+            d.x[a] = xa;
+            d.u[a] = p.u[a];
+            d.w[a] = p.omega[a];
+        }
+        d.d = p.diameter;
+        d.r = 0.5 * p.diameter;
+        d.rho = p.density;
+        d.fixed = p.fixed ? 1.0 : 0.0;
+        recs[i] = d;
+    }
+    if (n != h->np || !h->d_parts) {
+        h->np = n;
+        lbm_status st = alloc_particles(h, n);
+        if (st != LBM_OK) return st;
+    }
+    h->maxd = std::max(h->maxd, maxd);
+    if (remap)
+        CK(h, cudaMemcpyAsync(h->d_tmp, h->d_parts, sizeof(DevParticle) * n,
+                              cudaMemcpyDeviceToDevice, h->stream),
+           "particle copy");
+    if (n > 0) {
+        CK(h, cudaMemcpyAsync(h->d_parts, recs.data(), sizeof(DevParticle) * n,
+                              cudaMemcpyHostToDevice, h->stream),
+           "particle upload");
+        CK(h, cudaMemcpyAsync(h->d_prev, recs.data(), sizeof(DevParticle) * n,
+                              cudaMemcpyHostToDevice, h->stream),
+           "particle upload");
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "particle upload sync");  // recs is pageable
+    Launch L = base_launch(h);
+    CK(h, launch_regions(L), "region launch");
+    L.parts = h->d_prev;
+    CK(h, launch_regions(L), "region launch");
+    if (remap) {
+        L = base_launch(h);
+        L.box[0] = (int)std::ceil(h->maxd) + 4;
+        CK(h, launch_refill(h->storage, h->buf[1 - h->cur], h->buf[h->cur], L, h->d_tmp, h->d_parts, 0),
+           "refill launch");
+    }
+    h->have_particles = n > 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_particles(lbm_handle* h, lbm_particle* host_out) {
+    if (!h) return LBM_ERR_ARG;
+    if (h->np == 0) return read_status(h);
+    if (!host_out) return fail(h, LBM_ERR_ARG, "null output");
+    std::vector<DevParticle> recs((size_t)h->np);
+    CK(h, cudaMemcpyAsync(recs.data(), h->d_parts, sizeof(DevParticle) * h->np,
+                          cudaMemcpyDeviceToHost, h->stream),
+       "particle download");
+    lbm_status st = read_status(h);
+    for (int i = 0; i < h->np; ++i) {
+        lbm_particle& p = host_out[i];
+        for (int a = 0; a < 3; ++a) {
+            p.x[a] = recs[i].x[a];
+            p.u[a] = recs[i].u[a];
+            p.omega[a] = recs[i].w[a];
+        }
+        p.diameter = recs[i].d;
+        p.density = recs[i].rho;
+        p.fixed = recs[i].fixed != 0.0;
+    }
+    return st;
+}
+
+lbm_status lbm_init_equilibrium(lbm_handle* h, double rho, const double u[3]) {
+    if (!h || !u) return LBM_ERR_ARG;
+    if (!std::isfinite(rho) || !std::isfinite(u[0]) || !std::isfinite(u[1]) || !std::isfinite(u[2]))
+        return fail(h, LBM_ERR_ARG, "non-finite initial state");
+    Launch L = base_launch(h);
+    CK(h, launch_init_eq(h->storage, h->buf[h->cur], L, rho, u[0], u[1], u[2]), "init launch");
+    return after_pre_state(h);
+}
+
+lbm_status lbm_step(lbm_handle* h, int nsteps) {
+    if (!h || nsteps < 0) return LBM_ERR_ARG;
+    for (int i = 0; i < nsteps; ++i) {
+        lbm_status st = step_once(h);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_forces(lbm_handle* h, double* F, double* T) {
+    if (!h) return LBM_ERR_ARG;
+    if (h->np == 0) return read_status(h);
+    if (!F || !T) return fail(h, LBM_ERR_ARG, "null output");
+    CK(h, cudaMemcpyAsync(h->h_stage + 1, h->d_force, sizeof(double) * 6 * h->np,
+                          cudaMemcpyDeviceToHost, h->stream),
+       "force download");
+    lbm_status st = read_status(h);
+    for (int i = 0; i < h->np; ++i)
+        for (int a = 0; a < 3; ++a) {
+            F[3 * i + a] = h->h_stage[1 + 6 * i + a];
+            T[3 * i + a] = h->h_stage[1 + 6 * i + 3 + a];
+        }
+    return st;
+}
+
+lbm_status lbm_get_fields(lbm_handle* h, int what, void* dst, size_t bytes, int dst_is_device) {
+    if (!h || !dst) return LBM_ERR_ARG;
+    const size_t n = (size_t)h->g.n;
+    size_t need;
+    switch (what) {
+        case LBM_FIELD_PDF: need = (size_t)NQ * n * h->esize; break;
+        case LBM_FIELD_RHO:
+        case LBM_FIELD_EPS: need = n * sizeof(double); break;
+        case LBM_FIELD_U: need = 3 * n * sizeof(double); break;
+        case LBM_FIELD_FLAG: need = n * sizeof(int); break;
+        default: return fail(h, LBM_ERR_ARG, "unknown field");
+    }
+    if (bytes != need) return fail(h, LBM_ERR_ARG, "byte count does not match the field");
+    if (what == LBM_FIELD_PDF) {
+        CK(h, cudaMemcpyAsync(dst, h->buf[h->cur], need,
+                              dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              h->stream),
+           "field copy");
+        return read_status(h);
+    }
+    void* out = dst;
+    if (!dst_is_device) CK(h, cudaMalloc(&out, need), "cudaMalloc field");
+    Launch L = base_launch(h);
+    L.nostream = h->pending_pre;
+    cudaError_t e = launch_macro(h->storage, h->buf[h->cur], L, what, out);
+    if (e == cudaSuccess && !dst_is_device)
+        e = cudaMemcpyAsync(dst, out, need, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (!dst_is_device) cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(h, e, "field kernel");
+    return read_status(h);
+}
+
+lbm_status lbm_set_fields(lbm_handle* h, int what, const void* src, size_t bytes, int src_is_device) {
+    if (!h || !src) return LBM_ERR_ARG;
+    const size_t n = (size_t)h->g.n;
+    if (what == LBM_FIELD_PDF) {
+        const size_t need = (size_t)NQ * n * h->esize;
+        if (bytes != need) return fail(h, LBM_ERR_ARG, "byte count does not match the field");
+        CK(h, cudaMemcpyAsync(h->buf[h->cur], src, need,
+                              src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              h->stream),
+           "field copy");
+        CK(h, cudaStreamSynchronize(h->stream), "field copy sync");
+        h->pending_pre = 0;
+        return LBM_OK;
+    }
+    if (what == LBM_FIELD_PDF_PRE) {
+        const size_t need = (size_t)NQ * n * sizeof(double);
+        if (bytes != need) return fail(h, LBM_ERR_ARG, "byte count does not match the field");
+        const double* dsrc = (const double*)src;
+        double* tmp = nullptr;
+        if (!src_is_device) {
+            CK(h, cudaMalloc(&tmp, need), "cudaMalloc staging");
+            cudaError_t e = cudaMemcpyAsync(tmp, src, need, cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) {
+                cudaFree(tmp);
+                return cuda_fail(h, e, "field upload");
+            }
+            dsrc = tmp;
+        }
+        cudaError_t e = launch_from_f64(h->storage, dsrc, h->buf[h->cur], (long long)NQ * (long long)n,
+                                        h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (tmp) cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_fail(h, e, "field conversion");
+        return after_pre_state(h);
+    }
+    return fail(h, LBM_ERR_ARG, "field cannot be set");
+}
+
+lbm_status lbm_synchronize(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    return read_status(h);
+}
+
+lbm_status lbm_profile_enable(lbm_handle* h, int enable) {
+    if (!h) return LBM_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream), "profile sync");
+    for (auto& p : h->events) {
+        h->pool.push_back(p.a);
+        h->pool.push_back(p.b);
+    }
+    h->events.clear();
+    h->profiling = enable ? 1 : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_handle* h, int n_classes, double* ms, long long* launches) {
+    if (!h || n_classes < 0 || (n_classes > 0 && (!ms || !launches))) return LBM_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream), "profile sync");
+    for (int k = 0; k < n_classes; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (auto& p : h->events) {
+        float t = 0.0f;
+        CK(h, cudaEventElapsedTime(&t, p.a, p.b), "event elapsed");
+        if (p.cls < n_classes) {
+            ms[p.cls] += t;
+            launches[p.cls] += 1;
+        }
+    }
+    return LBM_OK;
+}
+
+}  // extern "C"

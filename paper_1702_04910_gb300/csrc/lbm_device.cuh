@@ -1,0 +1,522 @@
+// Device-side building blocks of the coupled D3Q19 sweep (sm_103a).
+//
+// Method: Rettinger & Ruede, arXiv:1702.04910, Sec. 2.  The sweep is the
+// pull form of Eq. (1)-(2): each cell gathers the post-collision values of
+// its upstream neighbours (stream, Eq. (2)), applies the wall / particle
+// boundary conditions on the links it pulls across (Eq. (12), (14)),
+// collides (Eq. (1) with Eq. (5) or (9), forcing Eq. (7); PSM Eq. (20)-(26))
+// and writes its own 19 post-collision values.  The stored state between
+// sweeps is therefore the post-collision field f~.
+//
+// Layout: structure of arrays f[q][z][y][x] (x fastest) so that a warp of
+// 32 consecutive x reads and writes 32 consecutive elements per direction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmgpu {
+
+constexpr int NQ = 19;
+constexpr int MAX_PARTICLES = 32;   // particle records staged in shared memory
+constexpr int CELL_SLOTS = 2;       // objects that may touch one cell (Sec. 2.3, multi-object cells)
+constexpr double NEAR_HALO = 2.0;   // cells around a sphere handled by the coupling kernels
+
+// ---- D3Q19 velocity set (Sec. 2.1): rest, 6 axis, 12 diagonals in pairs ----
+__host__ __device__ constexpr int cx(int q) {
+    constexpr int t[NQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[q];
+}
+__host__ __device__ constexpr int cy(int q) {
+    constexpr int t[NQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[q];
+}
+__host__ __device__ constexpr int cz(int q) {
+    constexpr int t[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[q];
+}
+__host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr double wq(int q) {
+    return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Particle record in device memory (160 B).  `reg` caches the near-particle
+// region of the current state (see axis_range): per axis {cell start, cell
+// count, tile start, tile count}, recomputed whenever the state changes.
+struct DevParticle {
+    double x[3], u[3], w[3];
+    double d, r, rho, fixed;
+    double pad;
+    int reg[12];
+    int pad2[2];
+};
+
+// Lattice geometry and tiling.  A tile is one thread block: tx * ty cells in
+// one z plane.
+struct Geom {
+    int nx, ny, nz;
+    int bc_z;           // 1: closed resting walls at z = 0 and z = nz
+    long long n;        // cells
+    int tx, ty;         // tile extent (= block dims)
+    int ntx, nty, ntz;  // tiles per axis
+};
+
+// Collision constants in the arithmetic type C.
+template <typename C>
+struct Coll {
+    C lam_p, lam_m;   // lambda_+ = -1/tau, lambda_- from Eq. (11)
+    C rho0, inv_rho0;
+    C fx, fy, fz;     // f_ext
+    int has_force;
+    // folded constants of the pair update (see collide_fluid)
+    C alpha, beta;    // 1 + (l+ + l-)/2, (l+ - l-)/2
+    C c0;             // 1 + l+
+    C m15r0;          // -3/2 rho0
+    C lpw[3];         // l+ w_k, k = rest, axis, diagonal
+    C k1w[3];         // 9/2 l+ w_k rho0
+    C k2w[3];         // 3 l- w_k rho0
+    C hw[3];          // 3 w_k (times U.f_ext)
+    C gq[10];         // 9 w_q (c_q . f_ext), q = 1,3,...,17 (index (q-1)/2)
+    C fq[10];         // 3 w_q (c_q . f_ext)
+};
+
+// Coupling constants (FP64: solid fractions, weights, forces).
+struct Coupl {
+    int kind;         // 0 none, 1 PSM, 2 MEM
+    int variant;      // PSM: 0 M1B1, 1 M2B2, 2 M3B2; MEM: 0 BB, 1 CLI
+    int np;
+    int subsample;
+    double tau;
+    double rho0;
+};
+
+// ---------------------------------------------------------------------------
+// Exactly rounded FP64 helpers for geometric predicates: these must give the
+// same bits on every machine, so no contraction into fused multiply-adds.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// Minimum-image separation along an axis of length L (periodic) or plain.
+__device__ __forceinline__ double min_image(double d, double L, bool periodic) {
+    if (!periodic) return d;
+    double h = mul_rn(0.5, L);
+    if (d > h) d = sub_rn(d, L);
+    else if (d < -h) d = add_rn(d, L);
+    return d;
+}
+
+__device__ __forceinline__ void separation(const Geom& g, double ax, double ay, double az,
+                                           const DevParticle& P, double& dx, double& dy,
+                                           double& dz) {
+    dx = min_image(sub_rn(ax, P.x[0]), (double)g.nx, true);
+    dy = min_image(sub_rn(ay, P.x[1]), (double)g.ny, true);
+    dz = min_image(sub_rn(az, P.x[2]), (double)g.nz, !g.bc_z);
+}
+
+__device__ __forceinline__ double norm2_rn(double dx, double dy, double dz) {
+    return add_rn(add_rn(mul_rn(dx, dx), mul_rn(dy, dy)), mul_rn(dz, dz));
+}
+
+// Point inside or on the sphere (MEM binary mapping, supersampling samples).
+__device__ __forceinline__ bool point_inside(const Geom& g, const DevParticle& P, double px,
+                                             double py, double pz) {
+    double dx, dy, dz;
+    separation(g, px, py, pz, P, dx, dy, dz);
+    return norm2_rn(dx, dy, dz) <= mul_rn(P.r, P.r);
+}
+
+__device__ __forceinline__ bool cell_inside(const Geom& g, const DevParticle& P, int x, int y,
+                                            int z) {
+    return point_inside(g, P, x + 0.5, y + 0.5, z + 0.5);
+}
+
+// Owner of a cell under a particle set: 0 fluid, s+1 inside particle s.
+__device__ __forceinline__ int cell_owner(const Geom& g, const DevParticle* parts, int np, int x,
+                                          int y, int z) {
+    for (int s = 0; s < np; ++s)
+        if (cell_inside(g, parts[s], x, y, z)) return s + 1;
+    return 0;
+}
+
+// Rigid-body velocity Eq. (13) at point p (minimum-image lever arm).
+__device__ __forceinline__ void body_velocity(const Geom& g, const DevParticle& P, double px,
+                                              double py, double pz, double& vx, double& vy,
+                                              double& vz) {
+    double rx, ry, rz;
+    separation(g, px, py, pz, P, rx, ry, rz);
+    vx = P.u[0] + (P.w[1] * rz - P.w[2] * ry);
+    vy = P.u[1] + (P.w[2] * rx - P.w[0] * rz);
+    vz = P.u[2] + (P.w[0] * ry - P.w[1] * rx);
+}
+
+// ---- near-particle regions -------------------------------------------------
+// Along one axis, the cells whose centre lies within R + NEAR_HALO of the
+// particle centre form a (possibly wrapped) cell range; the tiles holding
+// them form a (possibly wrapped) tile range [lo, lo+len) mod nt.
+struct AxisRange {
+    int clo, clen;  // cell range start (wrapped) and length
+    int tlo, tlen;  // tile range start (wrapped) and length
+};
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+    int q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+__device__ __forceinline__ int wrap_i(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ inline AxisRange axis_range(double X, double R, int ncell, int T, int nt,
+                                       bool periodic) {
+    AxisRange r;
+    // cells i with |i + 1/2 - X| <= R + halo  ->  i in [ceil(X-R-h-1/2), floor(X+R+h-1/2)]
+    int lo = (int)ceil(X - R - NEAR_HALO - 0.5);
+    int hi = (int)floor(X + R + NEAR_HALO - 0.5);
+    if (!periodic) {
+        lo = lo < 0 ? 0 : lo;
+        hi = hi > ncell - 1 ? ncell - 1 : hi;
+        r.clo = lo;
+        r.clen = hi >= lo ? hi - lo + 1 : 0;
+        if (r.clen == 0) {
+            r.tlo = 0;
+            r.tlen = 0;
+            return r;
+        }
+        r.tlo = lo / T;
+        r.tlen = hi / T - lo / T + 1;
+        return r;
+    }
+    int len = hi - lo + 1;
+    if (len >= ncell) {
+        r.clo = 0;
+        r.clen = ncell;
+        r.tlo = 0;
+        r.tlen = nt;
+        return r;
+    }
+    int wlo = wrap_i(lo, ncell), whi = wrap_i(hi, ncell);
+    r.clo = wlo;
+    r.clen = len;
+    int a = wlo / T, b = whi / T;
+    r.tlo = a;
+    r.tlen = wrap_i(b - a, nt) + 1;
+    if (wlo > whi && a == b) r.tlen = nt;  // wrapped range re-entering its own tile
+    return r;
+}
+
+__device__ __forceinline__ bool in_range(int i, int lo, int len, int n) {
+    return wrap_i(i - lo, n) < len;
+}
+
+struct NearRegion {
+    AxisRange ax[3];
+};
+
+__device__ inline NearRegion near_region(const Geom& g, const DevParticle& P) {
+    NearRegion nr;
+    nr.ax[0] = axis_range(P.x[0], P.r, g.nx, g.tx, g.ntx, true);
+    nr.ax[1] = axis_range(P.x[1], P.r, g.ny, g.ty, g.nty, true);
+    nr.ax[2] = axis_range(P.x[2], P.r, g.nz, 1, g.ntz, !g.bc_z);
+    return nr;
+}
+
+__device__ __forceinline__ bool tile_in_region(const Geom& g, const NearRegion& nr, int tx,
+                                               int ty, int tz) {
+    return in_range(tx, nr.ax[0].tlo, nr.ax[0].tlen, g.ntx) &&
+           in_range(ty, nr.ax[1].tlo, nr.ax[1].tlen, g.nty) &&
+           in_range(tz, nr.ax[2].tlo, nr.ax[2].tlen, g.ntz);
+}
+
+__device__ __forceinline__ bool cell_in_region(const Geom& g, const NearRegion& nr, int x, int y,
+                                               int z) {
+    return in_range(x, nr.ax[0].clo, nr.ax[0].clen, g.nx) &&
+           in_range(y, nr.ax[1].clo, nr.ax[1].clen, g.ny) &&
+           in_range(z, nr.ax[2].clo, nr.ax[2].clen, g.nz);
+}
+
+// Cache the region of P's current state in P.reg.
+__device__ inline void store_region(const Geom& g, DevParticle& P) {
+    NearRegion nr = near_region(g, P);
+    for (int a = 0; a < 3; ++a) {
+        P.reg[4 * a + 0] = nr.ax[a].clo;
+        P.reg[4 * a + 1] = nr.ax[a].clen;
+        P.reg[4 * a + 2] = nr.ax[a].tlo;
+        P.reg[4 * a + 3] = nr.ax[a].tlen;
+    }
+}
+
+__device__ __forceinline__ bool tile_in_reg(const Geom& g, const int* reg, int tx, int ty,
+                                            int tz) {
+    return in_range(tx, reg[2], reg[3], g.ntx) && in_range(ty, reg[6], reg[7], g.nty) &&
+           in_range(tz, reg[10], reg[11], g.ntz);
+}
+
+__device__ __forceinline__ bool cell_in_reg(const Geom& g, const int* reg, int x, int y, int z) {
+    return in_range(x, reg[0], reg[1], g.nx) && in_range(y, reg[4], reg[5], g.ny) &&
+           in_range(z, reg[8], reg[9], g.nz);
+}
+
+// ---- pull (stream, Eq. (2)) ---------------------------------------------------
+// Neighbour coordinates of a cell along -c_q (the upstream cell), with periodic
+// wrap in x, y (and z if periodic).  zs is out of [0,nz) at a closed wall.
+struct Nbr {
+    int xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Geom& g, int x, int y, int z) {
+    Nbr b;
+    b.xm = x == 0 ? g.nx - 1 : x - 1;
+    b.xp = x == g.nx - 1 ? 0 : x + 1;
+    b.ym = y == 0 ? g.ny - 1 : y - 1;
+    b.yp = y == g.ny - 1 ? 0 : y + 1;
+    if (g.bc_z) {
+        b.zm = z - 1;
+        b.zp = z + 1;
+    } else {
+        b.zm = z == 0 ? g.nz - 1 : z - 1;
+        b.zp = z == g.nz - 1 ? 0 : z + 1;
+    }
+    return b;
+}
+
+// Coordinates of x + k * c (k = +1 or -1) for a lattice direction q.
+template <int Q>
+__device__ __forceinline__ void shifted(const Nbr& b, int x, int y, int z, int sign, int& xs,
+                                        int& ys, int& zs) {
+    const int dx = sign * cx(Q), dy = sign * cy(Q), dz = sign * cz(Q);
+    xs = dx > 0 ? b.xp : (dx < 0 ? b.xm : x);
+    ys = dy > 0 ? b.yp : (dy < 0 ? b.ym : y);
+    zs = dz > 0 ? b.zp : (dz < 0 ? b.zm : z);
+}
+
+__device__ __forceinline__ long long lin(const Geom& g, int x, int y, int z) {
+    return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+}
+
+template <typename T>
+__device__ __forceinline__ double ld(const T* p) {
+    return (double)__ldg(p);
+}
+
+// Plain pull of all 19 values for a fluid cell that has no particle link:
+// periodic neighbours, halfway bounce-back at resting closed walls.
+template <typename T, typename C, int Q>
+__device__ __forceinline__ void pull_one(const T* __restrict__ src, const Geom& g, const Nbr& b,
+                                         int x, int y, int z, long long idx, C (&f)[NQ]) {
+    int xs, ys, zs;
+    shifted<Q>(b, x, y, z, -1, xs, ys, zs);
+    if (cz(Q) != 0 && (zs < 0 || zs >= g.nz)) {
+        f[Q] = (C)__ldg(src + (long long)opp(Q) * g.n + idx);
+    } else {
+        f[Q] = (C)__ldg(src + (long long)Q * g.n + lin(g, xs, ys, zs));
+    }
+}
+
+template <typename T, typename C, int Q>
+struct PullAll {
+    __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
+                                               const Nbr& b, int x, int y, int z, long long idx,
+                                               C (&f)[NQ]) {
+        pull_one<T, C, Q>(src, g, b, x, y, z, idx, f);
+        PullAll<T, C, Q + 1>::run(src, g, b, x, y, z, idx, f);
+    }
+};
+template <typename T, typename C>
+struct PullAll<T, C, NQ> {
+    __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const Nbr&, int,
+                                               int, int, long long, C (&)[NQ]) {}
+};
+
+template <typename T, typename C>
+__device__ __forceinline__ void pull_plain(const T* __restrict__ src, const Geom& g, int x, int y,
+                                           int z, long long idx, C (&f)[NQ]) {
+    Nbr b = make_nbr(g, x, y, z);
+    PullAll<T, C, 0>::run(src, g, b, x, y, z, idx, f);
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void load_own(const T* __restrict__ src, const Geom& g, long long idx,
+                                         C (&f)[NQ]) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) f[q] = (C)__ldg(src + (long long)q * g.n + idx);
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void store_own(T* __restrict__ dst, const Geom& g, long long idx,
+                                          const C (&f)[NQ]) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + idx] = (T)f[q];
+}
+
+// ---- moments Eq. (4) ---------------------------------------------------------
+template <typename C>
+__device__ __forceinline__ void moments(const C (&f)[NQ], const Coll<C>& k, C& rho, C& ux, C& uy,
+                                        C& uz) {
+    C s1 = f[1] + f[2], s3 = f[3] + f[4], s5 = f[5] + f[6], s7 = f[7] + f[8];
+    C s9 = f[9] + f[10], s11 = f[11] + f[12], s13 = f[13] + f[14], s15 = f[15] + f[16];
+    C s17 = f[17] + f[18];
+    rho = f[0] + ((s1 + s3) + (s5 + s7)) + ((s9 + s11) + (s13 + s15)) + s17;
+    C d1 = f[1] - f[2], d3 = f[3] - f[4], d5 = f[5] - f[6], d7 = f[7] - f[8];
+    C d9 = f[9] - f[10], d11 = f[11] - f[12], d13 = f[13] - f[14], d15 = f[15] - f[16];
+    C d17 = f[17] - f[18];
+    ux = ((d1 + d7) + (d9 + d11) + d13) * k.inv_rho0;
+    uy = ((d3 + d7) - (d9 - d15) + d17) * k.inv_rho0;
+    uz = ((d5 + d11) - (d13 - d15) - d17) * k.inv_rho0;
+}
+
+// ---- fluid collision Eq. (1) with TRT Eq. (9)-(10) (BGK: lambda_- = lambda_+)
+// and forcing Eq. (7), in place, written per opposite pair (q, qbar):
+//   f^eq,+ = w (rho + rho0 (9/2 (c.U)^2 - 3/2 U.U)),  f^eq,- = 3 w rho0 c.U,
+//   F^+ = w (9 (c.U)(c.f) - 3 U.f),                   F^- = 3 w c.f.
+// The per-pair update is written with the relaxation folded in:
+//   f_q'    = alpha f_q    + beta f_qbar - (P + M)
+//   f_qbar' = alpha f_qbar + beta f_q    - (P - M)
+// with P = l+ f^eq,+ - F^+ and M = l- f^eq,- - F^-, which expands
+// f_q + l+ (f_q^+ - f^eq,+) + l- (f_q^- - f^eq,-) + F_q exactly.
+template <typename C, int Q, int K, bool FORCE>
+__device__ __forceinline__ void trt_pair(C (&f)[NQ], C cu, const C (&bw)[3], const Coll<C>& k) {
+    constexpr int QB = Q + 1;
+    C P = FORCE ? fma(k.k1w[K], cu * cu, fma(-k.gq[(Q - 1) / 2], cu, bw[K]))
+                : fma(k.k1w[K], cu * cu, bw[K]);
+    C M = FORCE ? fma(k.k2w[K], cu, -k.fq[(Q - 1) / 2]) : k.k2w[K] * cu;
+    const C a = f[Q], b = f[QB];
+    f[Q] = fma(k.alpha, a, fma(k.beta, b, -(P + M)));
+    f[QB] = fma(k.alpha, b, fma(k.beta, a, -(P - M)));
+}
+
+template <typename C, bool FORCE>
+__device__ __forceinline__ void collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
+    C rho, ux, uy, uz;
+    moments(f, k, rho, ux, uy, uz);
+    const C uu = fma(ux, ux, fma(uy, uy, uz * uz));
+    const C base = fma(k.m15r0, uu, rho);
+    C bw[3];
+    if (FORCE) {
+        const C uf = fma(ux, k.fx, fma(uy, k.fy, uz * k.fz));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bw[c] = fma(k.lpw[c], base, k.hw[c] * uf);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bw[c] = k.lpw[c] * base;
+    }
+    f[0] = fma(k.c0, f[0], -bw[0]);
+    trt_pair<C, 1, 1, FORCE>(f, ux, bw, k);
+    trt_pair<C, 3, 1, FORCE>(f, uy, bw, k);
+    trt_pair<C, 5, 1, FORCE>(f, uz, bw, k);
+    trt_pair<C, 7, 2, FORCE>(f, ux + uy, bw, k);
+    trt_pair<C, 9, 2, FORCE>(f, ux - uy, bw, k);
+    trt_pair<C, 11, 2, FORCE>(f, ux + uz, bw, k);
+    trt_pair<C, 13, 2, FORCE>(f, ux - uz, bw, k);
+    trt_pair<C, 15, 2, FORCE>(f, uy + uz, bw, k);
+    trt_pair<C, 17, 2, FORCE>(f, uy - uz, bw, k);
+}
+
+// Fluid collision Eq. (1) with TRT Eq. (9)-(10) (BGK: lambda_- = lambda_+)
+// and forcing Eq. (7), in place.
+template <typename C>
+__device__ __forceinline__ void collide_fluid(C (&f)[NQ], const Coll<C>& k) {
+    if (k.has_force)
+        collide_fluid_t<C, true>(f, k);
+    else
+        collide_fluid_t<C, false>(f, k);
+}
+
+// Collision operator values C_q (Eq. (5)/(9)) and forcing F_q (Eq. (7)) as
+// separate arrays, for the PSM blend Eq. (26).  Also returns rho and U.
+template <typename C>
+__device__ inline void fluid_operator(const C (&f)[NQ], const Coll<C>& k, C (&Cf)[NQ],
+                                      C (&Fq)[NQ], C& rho, C& ux, C& uy, C& uz) {
+    moments(f, k, rho, ux, uy, uz);
+    C uu = ux * ux + uy * uy + uz * uz;
+    C base = rho - (C)1.5 * k.rho0 * uu;
+    C uf = ux * k.fx + uy * k.fy + uz * k.fz;
+    Cf[0] = k.lam_p * (f[0] - (C)(1.0 / 3.0) * base);
+    Fq[0] = (C)(1.0 / 3.0) * ((C)-3 * uf);
+#pragma unroll
+    for (int q = 1; q < NQ; q += 2) {
+        const C w = (C)wq(q);
+        C cu = (C)cx(q) * ux + (C)cy(q) * uy + (C)cz(q) * uz;
+        C cf = (C)cx(q) * k.fx + (C)cy(q) * k.fy + (C)cz(q) * k.fz;
+        C fs = f[q] + f[q + 1], fd = f[q] - f[q + 1];
+        C eqs = w * (base + (C)4.5 * k.rho0 * cu * cu);
+        C eqd = (C)3 * w * k.rho0 * cu;
+        C cs = k.lam_p * ((C)0.5 * fs - eqs);
+        C cd = k.lam_m * ((C)0.5 * fd - eqd);
+        Cf[q] = cs + cd;
+        Cf[q + 1] = cs - cd;
+        C fsym = w * ((C)9 * cu * cf - (C)3 * uf);
+        C fanti = (C)3 * w * cf;
+        Fq[q] = fsym + fanti;
+        Fq[q + 1] = fsym - fanti;
+    }
+}
+
+// Equilibrium Eq. (3) for all q at density rho and velocity (vx, vy, vz).
+template <typename C>
+__device__ __forceinline__ void equilibrium(C rho, C vx, C vy, C vz, C rho0, C (&e)[NQ]) {
+    C base = rho - (C)1.5 * rho0 * (vx * vx + vy * vy + vz * vz);
+    e[0] = (C)(1.0 / 3.0) * base;
+#pragma unroll
+    for (int q = 1; q < NQ; q += 2) {
+        const C w = (C)wq(q);
+        C cu = (C)cx(q) * vx + (C)cy(q) * vy + (C)cz(q) * vz;
+        C s = w * (base + (C)4.5 * rho0 * cu * cu);
+        C d = (C)3 * w * rho0 * cu;
+        e[q] = s + d;
+        e[q + 1] = s - d;
+    }
+}
+
+// ---- PSM solid fraction: n^3 supersampling (Sec. 2.3) -----------------------
+// Cells wholly inside the sphere give 1 and cells whose box misses the sphere
+// give 0 without sampling; both short-cuts agree exactly with the sampled
+// count (samples lie at least 1/(2n) inside the cell, far beyond rounding).
+__device__ inline double solid_fraction(const Geom& g, const DevParticle& P, int x, int y, int z,
+                                        int n) {
+    double dx, dy, dz;
+    separation(g, x + 0.5, y + 0.5, z + 0.5, P, dx, dy, dz);
+    double ax = fabs(dx), ay = fabs(dy), az = fabs(dz);
+    double nxd = fmax(ax - 0.5, 0.0), nyd = fmax(ay - 0.5, 0.0), nzd = fmax(az - 0.5, 0.0);
+    double R2 = mul_rn(P.r, P.r);
+    if (norm2_rn(nxd, nyd, nzd) > R2 * (1.0 + 1e-12) + 1e-9) return 0.0;
+    double fxd = ax + 0.5, fyd = ay + 0.5, fzd = az + 0.5;
+    if (norm2_rn(fxd, fyd, fzd) < R2 * (1.0 - 1e-12) - 1e-9) return 1.0;
+    int inside = 0;
+    for (int k = 0; k < n; ++k) {
+        double pz = z + (k + 0.5) / n;
+        for (int j = 0; j < n; ++j) {
+            double py = y + (j + 0.5) / n;
+            for (int i = 0; i < n; ++i) {
+                double px = x + (i + 0.5) / n;
+                inside += point_inside(g, P, px, py, pz) ? 1 : 0;
+            }
+        }
+    }
+    return (double)inside / ((double)n * n * n);
+}
+
+// ---- MEM link geometry ---------------------------------------------------------
+// delta: smallest root t of |x + t c - X| = R, clamped to [0, 1].
+__device__ inline double link_delta(const Geom& g, const DevParticle& P, double px, double py,
+                                    double pz, int ccx, int ccy, int ccz) {
+    double dx, dy, dz;
+    separation(g, px, py, pz, P, dx, dy, dz);
+    double a = (double)(ccx * ccx + ccy * ccy + ccz * ccz);
+    double b = dx * ccx + dy * ccy + dz * ccz;
+    double c = (dx * dx + dy * dy + dz * dz) - P.r * P.r;
+    double disc = b * b - a * c;
+    if (disc < 0.0) disc = 0.0;
+    double t = (-b - sqrt(disc)) / a;
+    return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+}
+
+// ---- block reductions (FP64) --------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace lbmgpu

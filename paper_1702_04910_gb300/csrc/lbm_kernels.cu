@@ -1,0 +1,834 @@
+// Kernels of the coupled D3Q19 step and their launchers (sm_103a).
+//
+// One global step (Algorithm 1 / Algorithm 2 of Rettinger & Ruede,
+// arXiv:1702.04910) is built from:
+//   k_bulk      fused pull stream + fluid collision for every tile that no
+//               particle comes near (the whole domain but an O(D^3) box);
+//   k_near      the same for the tiles near a particle, with the coupling:
+//               PSM solid fractions and weighted collision Eq. (20)-(26) and
+//               force/torque Eq. (28)-(29), or MEM link boundary conditions
+//               Eq. (12)/(14) and link forces Eq. (16); per-tile force
+//               partials reduced warp -> block in a fixed order;
+//   k_finalize  fixed-order sum of the tile partials, subcycle average;
+//   k_rigid     explicit Euler rigid-body update;
+//   k_refill    MEM re-mapping: PDF reconstruction Eq. (19) of uncovered
+//               cells, then their collision.
+#include <cuda_runtime.h>
+
+#include "lbm_launch.h"
+
+namespace lbmgpu {
+
+// ---------------------------------------------------------------------------
+// per-cell force/torque slots (a cell may touch up to CELL_SLOTS particles)
+struct Slots {
+    int id[CELL_SLOTS];
+    double v[CELL_SLOTS][6];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int s = 0; s < CELL_SLOTS; ++s) {
+            id[s] = -1;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) v[s][c] = 0.0;
+        }
+    }
+    // returns false when every slot is taken by other particles
+    __device__ __forceinline__ bool add(int p, const double (&F)[3], const double (&T)[3]) {
+#pragma unroll
+        for (int s = 0; s < CELL_SLOTS; ++s) {
+            if (id[s] == p || id[s] < 0) {
+                id[s] = p;
+                v[s][0] += F[0];
+                v[s][1] += F[1];
+                v[s][2] += F[2];
+                v[s][3] += T[0];
+                v[s][4] += T[1];
+                v[s][5] += T[2];
+                return true;
+            }
+        }
+        return false;
+    }
+    __device__ __forceinline__ double get(int p, int c) const {
+        double r = 0.0;
+#pragma unroll
+        for (int s = 0; s < CELL_SLOTS; ++s)
+            if (id[s] == p) r += v[s][c];
+        return r;
+    }
+};
+
+__device__ __forceinline__ void cross3(const double (&a)[3], const double (&b)[3],
+                                       double (&r)[3]) {
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// ---------------------------------------------------------------------------
+// MEM pull for a fluid cell: stream Eq. (2); links whose upstream cell is
+// solid take the boundary value Eq. (12) (BB) or Eq. (14) (CLI); resting
+// closed walls take halfway bounce-back.  When `slots` is non-null the link
+// force Eq. (16) and its torque about X_p (arm x_b - X_p) are accumulated.
+//
+// In pull form the link of the paper (fluid x, solid neighbour x + c_qp)
+// appears while filling direction q = qbar_p: the upstream cell x - c_q is
+// x + c_qp.
+template <typename T, typename C, int Q>
+__device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Geom& g,
+                                             const Coupl& cp, const DevParticle* parts, int np,
+                                             const Nbr& b, int x, int y, int z, long long idx,
+                                             C (&f)[NQ], Slots* slots, int* status) {
+    constexpr int QP = opp(Q);  // paper's link direction (towards the solid cell)
+    int xs, ys, zs;
+    shifted<Q>(b, x, y, z, -1, xs, ys, zs);
+    if (cz(Q) != 0 && (zs < 0 || zs >= g.nz)) {
+        f[Q] = (C)__ldg(src + (long long)QP * g.n + idx);
+        return;
+    }
+    int owner = 0;
+    for (int s = 0; s < np; ++s) {
+        if (!cell_in_reg(g, parts[s].reg, x, y, z)) continue;
+        if (cell_inside(g, parts[s], xs, ys, zs)) {
+            owner = s + 1;
+            break;
+        }
+    }
+    if (!owner) {
+        f[Q] = (C)__ldg(src + (long long)Q * g.n + lin(g, xs, ys, zs));
+        return;
+    }
+    const DevParticle& P = parts[owner - 1];
+    const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
+    const double delta =
+        cp.variant == 0 ? 0.5 : link_delta(g, P, xc, yc, zc, cx(QP), cy(QP), cz(QP));
+    const double xb[3] = {xc + delta * cx(QP), yc + delta * cy(QP), zc + delta * cz(QP)};
+    double v[3];
+    body_velocity(g, P, xb[0], xb[1], xb[2], v[0], v[1], v[2]);
+    const double vc = v[0] * cx(QP) + v[1] * cy(QP) + v[2] * cz(QP);
+    const double ftqp = ld(src + (long long)QP * g.n + idx);  // f~_qp(x)
+    const double wr = 3.0 * wq(QP) * cp.rho0;                 // w_q / c_s^2 * rho0
+    double val;
+    bool cli_done = false;
+    if (cp.variant == 1) {
+        // second node x - c_qp = x + c_q must be a fluid cell
+        int x2, y2, z2;
+        shifted<Q>(b, x, y, z, +1, x2, y2, z2);
+        bool ok = !(cz(Q) != 0 && (z2 < 0 || z2 >= g.nz));
+        if (ok) {
+            for (int s = 0; s < np; ++s) {
+                if (!cell_in_reg(g, parts[s].reg, x, y, z)) continue;
+                if (cell_inside(g, parts[s], x2, y2, z2)) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        if (ok) {
+            const double k0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
+            const double alpha = 4.0 / (1.0 + 2.0 * delta);
+            const double f2 = ld(src + (long long)QP * g.n + lin(g, x2, y2, z2));
+            const double fq = ld(src + (long long)Q * g.n + idx);
+            val = ftqp + k0 * f2 - k0 * fq - alpha * wr * vc;
+            cli_done = true;
+        }
+    }
+    if (!cli_done) val = ftqp - 2.0 * wr * vc;
+    f[Q] = (C)val;
+    if (slots) {
+        double F[3], arm[3], Tq[3];
+        F[0] = (cx(QP) - v[0]) * ftqp - (cx(Q) - v[0]) * val;
+        F[1] = (cy(QP) - v[1]) * ftqp - (cy(Q) - v[1]) * val;
+        F[2] = (cz(QP) - v[2]) * ftqp - (cz(Q) - v[2]) * val;
+        separation(g, xb[0], xb[1], xb[2], P, arm[0], arm[1], arm[2]);
+        cross3(arm, F, Tq);
+        if (!slots->add(owner - 1, F, Tq)) atomicOr(status, ST_TOO_MANY_OBJECTS);
+    }
+}
+
+template <typename T, typename C, int Q>
+struct MemPull {
+    __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
+                                               const Coupl& cp, const DevParticle* parts, int np,
+                                               const Nbr& b, int x, int y, int z, long long idx,
+                                               C (&f)[NQ], Slots* slots, int* status) {
+        mem_pull_one<T, C, Q>(src, g, cp, parts, np, b, x, y, z, idx, f, slots, status);
+        MemPull<T, C, Q + 1>::run(src, g, cp, parts, np, b, x, y, z, idx, f, slots, status);
+    }
+};
+template <typename T, typename C>
+struct MemPull<T, C, NQ> {
+    __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const Coupl&,
+                                               const DevParticle*, int, const Nbr&, int, int, int,
+                                               long long, C (&)[NQ], Slots*, int*) {}
+};
+
+template <typename T, typename C>
+__device__ __forceinline__ void mem_pull(const T* __restrict__ src, const Geom& g, const Coupl& cp,
+                                         const DevParticle* parts, int np, int x, int y, int z,
+                                         long long idx, C (&f)[NQ], Slots* slots, int* status) {
+    Nbr b = make_nbr(g, x, y, z);
+    f[0] = (C)__ldg(src + idx);
+    MemPull<T, C, 1>::run(src, g, cp, parts, np, b, x, y, z, idx, f, slots, status);
+}
+
+// ---------------------------------------------------------------------------
+// PSM weighted collision Eq. (26) with C^PSM Eq. (20), B1/B2 Eq. (21)/(22),
+// M1/M2/M3 Eq. (23)-(25), force/torque Eq. (28)-(29).  `eps[k]` are the
+// solid fractions of particles `pid[k]` (k < nobj) at this cell.
+template <typename C>
+__device__ inline void psm_collide(C (&f)[NQ], const Coll<C>& k, const Coupl& cp, const Geom& g,
+                                   const DevParticle* parts, int nobj, const int (&pid)[CELL_SLOTS],
+                                   const double (&eps)[CELL_SLOTS], int x, int y, int z,
+                                   Slots& slots) {
+    C Cf[NQ], Fq[NQ], ssum[NQ], feqU[NQ];
+    C rho, ux, uy, uz;
+    fluid_operator(f, k, Cf, Fq, rho, ux, uy, uz);
+    equilibrium(rho, ux, uy, uz, k.rho0, feqU);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) ssum[q] = (C)0;
+    double B = 0.0;
+    const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
+    for (int o = 0; o < nobj; ++o) {
+        const DevParticle& P = parts[pid[o]];
+        const double e = eps[o];
+        const double Bs =
+            cp.variant == 0 ? e : e * (cp.tau - 0.5) / ((1.0 - e) + (cp.tau - 0.5));
+        B += Bs;
+        double v[3];
+        body_velocity(g, P, xc, yc, zc, v[0], v[1], v[2]);
+        C feqV[NQ];
+        equilibrium(rho, (C)v[0], (C)v[1], (C)v[2], k.rho0, feqV);
+        double Fs[3] = {0.0, 0.0, 0.0};
+        const C Bc = (C)Bs;
+        const C om = (C)(1.0 - 1.0 / cp.tau);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int qb = opp(q);
+            C cs;
+            if (cp.variant == 0)
+                cs = (f[qb] - feqU[qb]) - (f[q] - feqV[q]);
+            else if (cp.variant == 1)
+                cs = (feqV[q] - f[q]) + om * (f[q] - feqU[q]);
+            else
+                cs = (f[qb] - feqV[qb]) - (f[q] - feqV[q]);
+            ssum[q] += Bc * cs;
+            Fs[0] += (double)cs * cx(qb);
+            Fs[1] += (double)cs * cy(qb);
+            Fs[2] += (double)cs * cz(qb);
+        }
+        double F[3] = {Bs * Fs[0], Bs * Fs[1], Bs * Fs[2]}, arm[3], Tq[3];
+        separation(g, xc, yc, zc, P, arm[0], arm[1], arm[2]);
+        cross3(arm, F, Tq);
+        slots.add(pid[o], F, Tq);
+    }
+    const C oneB = (C)(1.0 - B);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) f[q] = f[q] + (oneB * Cf[q] + ssum[q]) + oneB * Fq[q];
+}
+
+// ---------------------------------------------------------------------------
+// bulk sweep: tiles no particle comes near
+template <typename T, typename C, bool NOSTREAM>
+__global__ void __launch_bounds__(256)
+    k_bulk(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k,
+           const DevParticle* __restrict__ parts, int np, int all_tiles) {
+    const int tX = blockIdx.x, tY = blockIdx.y, tZ = blockIdx.z;
+    if (!all_tiles) {
+        for (int s = 0; s < np; ++s)
+            if (tile_in_reg(g, parts[s].reg, tX, tY, tZ)) return;
+    }
+    const int x = tX * g.tx + threadIdx.x, y = tY * g.ty + threadIdx.y, z = tZ;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long idx = lin(g, x, y, z);
+    C f[NQ];
+    if (NOSTREAM)
+        load_own(src, g, idx, f);
+    else
+        pull_plain(src, g, x, y, z, idx, f);
+    collide_fluid(f, k);
+    store_own(dst, g, idx, f);
+}
+
+// ---------------------------------------------------------------------------
+// near-particle sweep.  Grid (box_x, box_y, box_z * np): block (kx, ky, kz)
+// of particle p handles tile (tlo + k) of p's region unless a lower-index
+// particle's region also holds that tile.
+template <typename T, typename C, int KIND, bool NOSTREAM>
+__global__ void __launch_bounds__(256)
+    k_near(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
+           const DevParticle* __restrict__ parts, double* __restrict__ partials,
+           int* __restrict__ status, int bz) {
+    __shared__ DevParticle sp[MAX_PARTICLES];
+    __shared__ double red[8][6];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    for (int i = tid; i < cp.np * (int)(sizeof(DevParticle) / sizeof(double)); i += nthr)
+        reinterpret_cast<double*>(sp)[i] = reinterpret_cast<const double*>(parts)[i];
+    __syncthreads();
+    const int p = blockIdx.z / bz, kz = blockIdx.z % bz, kx = blockIdx.x, ky = blockIdx.y;
+    const int* R = sp[p].reg;
+    if (kx >= R[3] || ky >= R[7] || kz >= R[11]) return;
+    const int tX = (R[2] + kx) % g.ntx, tY = (R[6] + ky) % g.nty, tZ = (R[10] + kz) % g.ntz;
+    for (int s = 0; s < p; ++s)
+        if (tile_in_reg(g, sp[s].reg, tX, tY, tZ)) return;
+
+    const int x = tX * g.tx + threadIdx.x, y = tY * g.ty + threadIdx.y, z = tZ;
+    const bool active = x < g.nx && y < g.ny;
+    Slots slots;
+    slots.clear();
+    if (active) {
+        const long long idx = lin(g, x, y, z);
+        C f[NQ];
+        if (KIND == 2) {
+            // MEM: solid cells are not updated (Sec. 2.2)
+            int own = 0;
+            for (int s = 0; s < cp.np && !own; ++s)
+                if (cell_in_reg(g, sp[s].reg, x, y, z) && cell_inside(g, sp[s], x, y, z))
+                    own = s + 1;
+            if (!own) {
+                if (NOSTREAM)
+                    load_own(src, g, idx, f);
+                else
+                    mem_pull(src, g, cp, sp, cp.np, x, y, z, idx, f, &slots, status);
+                collide_fluid(f, k);
+                store_own(dst, g, idx, f);
+            }
+        } else {
+            if (NOSTREAM)
+                load_own(src, g, idx, f);
+            else
+                pull_plain(src, g, x, y, z, idx, f);
+            int nobj = 0;
+            int pid[CELL_SLOTS];
+            double eps[CELL_SLOTS];
+            if (KIND == 1) {
+                for (int s = 0; s < cp.np; ++s) {
+                    if (!cell_in_reg(g, sp[s].reg, x, y, z)) continue;
+                    double e = solid_fraction(g, sp[s], x, y, z, cp.subsample);
+                    if (e <= 0.0) continue;
+                    if (nobj < CELL_SLOTS) {
+                        pid[nobj] = s;
+                        eps[nobj] = e;
+                        ++nobj;
+                    } else {
+                        atomicOr(status, ST_TOO_MANY_OBJECTS);
+                    }
+                }
+            }
+            if (nobj == 0)
+                collide_fluid(f, k);
+            else
+                psm_collide(f, k, cp, g, sp, nobj, pid, eps, x, y, z, slots);
+            store_own(dst, g, idx, f);
+        }
+    }
+    if (KIND == 0 || (NOSTREAM && KIND == 2)) return;
+    // fixed-order reduction of this tile's contribution for each particle
+    const int ntiles = g.ntx * g.nty * g.ntz;
+    const long long tile = (long long)tX + (long long)g.ntx * ((long long)tY + (long long)g.nty * tZ);
+    const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
+    for (int s = 0; s < cp.np; ++s) {
+        if (!tile_in_reg(g, sp[s].reg, tX, tY, tZ)) continue;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double v = warp_sum(slots.get(s, c));
+            if (lane == 0) red[warp][c] = v;
+        }
+        __syncthreads();
+        if (tid < 6) {
+            double acc = 0.0;
+            for (int w = 0; w < nwarp; ++w) acc += red[w][tid];
+            partials[((long long)s * ntiles + tile) * 6 + tid] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order force/torque total of particle p (one block per particle):
+// F = (S_1 + ... + S_nsub) / nsub with S_k the sum of the tile partials of
+// subcycle k over p's region.
+__global__ void __launch_bounds__(256)
+    k_finalize(Geom g, const DevParticle* __restrict__ parts, int np,
+               const double* __restrict__ partials, int nsub, double* __restrict__ out) {
+    __shared__ double red[256][6];
+    const int p = blockIdx.x, tid = threadIdx.x;
+    const int* R = parts[p].reg;
+    const long long count = (long long)R[3] * R[7] * R[11];
+    const int ntiles = g.ntx * g.nty * g.ntz;
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    for (int sub = 0; sub < nsub; ++sub) {
+        const double* base = partials + ((long long)sub * np + p) * ntiles * 6;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (long long kk = tid; kk < count; kk += blockDim.x) {
+            int kx = (int)(kk % R[3]);
+            int ky = (int)((kk / R[3]) % R[7]);
+            int kz = (int)(kk / ((long long)R[3] * R[7]));
+            int tX = (R[2] + kx) % g.ntx, tY = (R[6] + ky) % g.nty, tZ = (R[10] + kz) % g.ntz;
+            long long tile = (long long)tX + (long long)g.ntx * ((long long)tY + (long long)g.nty * tZ);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[c] += base[tile * 6 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) red[tid][c] = acc[c];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (tid < s)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) red[tid][c] += red[tid + s][c];
+            __syncthreads();
+        }
+        if (tid == 0)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) tot[c] += red[0][c];
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int c = 0; c < 6; ++c) out[p * 6 + c] = tot[c] / nsub;
+}
+
+// ---------------------------------------------------------------------------
+// explicit Euler rigid-body update over dt, gravity + buoyancy
+// (rho_p - rho0) V g; keeps the previous state in `prev`.
+__global__ void k_rigid(Geom g, DevParticle* __restrict__ parts, DevParticle* __restrict__ prev,
+                        int np, const double* __restrict__ force, double rho0, double gx,
+                        double gy, double gz, double dt, int wall_contact,
+                        int* __restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    DevParticle P = parts[p];
+    prev[p] = P;
+    if (P.fixed == 0.0) {
+        const double PI = 3.14159265358979323846;
+        const double D = P.d, R = 0.5 * D;
+        const double V = PI * D * D * D / 6.0;
+        const double m = P.rho * V, I = m * D * D / 10.0;
+        const double grav[3] = {gx, gy, gz};
+        double Ft[3];
+        for (int a = 0; a < 3; ++a) Ft[a] = force[p * 6 + a] + (P.rho - rho0) * V * grav[a];
+        for (int a = 0; a < 3; ++a) P.x[a] += dt * P.u[a];
+        for (int a = 0; a < 3; ++a) P.u[a] += dt * Ft[a] / m;
+        for (int a = 0; a < 3; ++a) P.w[a] += dt * force[p * 6 + 3 + a] / I;
+        const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+        for (int a = 0; a < 3; ++a) {
+            if (a == 2 && g.bc_z) continue;
+            if (P.x[a] < 0.0) P.x[a] += L[a];
+            else if (P.x[a] >= L[a]) P.x[a] -= L[a];
+        }
+        if (g.bc_z) {
+            if (wall_contact) {
+                if (P.x[2] - R < 1.0) {
+                    P.x[2] = R + 1.0;
+                    if (P.u[2] < 0.0) P.u[2] = 0.0;
+                }
+                if (P.x[2] + R > L[2] - 1.0) {
+                    P.x[2] = L[2] - 1.0 - R;
+                    if (P.u[2] > 0.0) P.u[2] = 0.0;
+                }
+            } else if (P.x[2] - R < 0.0 || P.x[2] + R > L[2]) {
+                atomicOr(status, ST_DOMAIN);
+            }
+        }
+    }
+    store_region(g, P);
+    parts[p] = P;
+}
+
+__global__ void k_regions(Geom g, DevParticle* parts, int np) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) store_region(g, parts[p]);
+}
+
+// ---------------------------------------------------------------------------
+// MEM re-mapping with PDF reconstruction (Sec. 2.2, Eq. (19)).  One thread per
+// cell of the box around each particle's old position.  A cell solid under
+// p_old (owner p) and fluid under p_new gets:
+//   extrapolate = 1: f = 3 f(x+c_n) - 3 f(x+2c_n) + f(x+3c_n) (fewer terms when
+//     fewer usable fluid cells follow), with the pre-collision values of those
+//     cells rebuilt from srcB (the buffer the last sweep pulled from) under
+//     p_old; then the velocity constraint j = rho0 v; with no usable cell,
+//     f_eq(rho_bar, v);
+//   extrapolate = 0: f_eq(rho0, v);
+// and is then collided (plain fluid collision) into dst.
+template <typename T, typename C>
+__global__ void __launch_bounds__(128)
+    k_refill(const T* __restrict__ srcB, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
+             const DevParticle* __restrict__ p_old, const DevParticle* __restrict__ p_new,
+             int extrapolate, int side, int* __restrict__ status) {
+    __shared__ DevParticle so[MAX_PARTICLES], sn[MAX_PARTICLES];
+    const int tid = threadIdx.x;
+    const int nd = cp.np * (int)(sizeof(DevParticle) / sizeof(double));
+    for (int i = tid; i < nd; i += blockDim.x) {
+        reinterpret_cast<double*>(so)[i] = reinterpret_cast<const double*>(p_old)[i];
+        reinterpret_cast<double*>(sn)[i] = reinterpret_cast<const double*>(p_new)[i];
+    }
+    __syncthreads();
+    const int p = blockIdx.y;
+    const long long lid = (long long)blockIdx.x * blockDim.x + tid;
+    if (lid >= (long long)side * side * side) return;
+    const int kx = (int)(lid % side), ky = (int)((lid / side) % side),
+              kz = (int)(lid / ((long long)side * side));
+    const DevParticle& Po = so[p];
+    int x = (int)floor(Po.x[0] - Po.r) - 1 + kx;
+    int y = (int)floor(Po.x[1] - Po.r) - 1 + ky;
+    int z = (int)floor(Po.x[2] - Po.r) - 1 + kz;
+    x = wrap_i(x, g.nx);
+    y = wrap_i(y, g.ny);
+    if (g.bc_z) {
+        if (z < 0 || z >= g.nz) return;
+    } else {
+        z = wrap_i(z, g.nz);
+    }
+    if (cell_owner(g, so, cp.np, x, y, z) != p + 1) return;
+    if (cell_owner(g, sn, cp.np, x, y, z) != 0) return;
+
+    const DevParticle& Pn = sn[p];
+    const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
+    double v[3];
+    body_velocity(g, Pn, xc, yc, zc, v[0], v[1], v[2]);
+    C fn[NQ];
+    int m = 0;
+    int qn = 1;
+    int nbx[3], nby[3], nbz[3];
+    if (extrapolate) {
+        double nrm[3];
+        separation(g, xc, yc, zc, Pn, nrm[0], nrm[1], nrm[2]);
+        double len = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        if (len > 0.0)
+            for (int a = 0; a < 3; ++a) nrm[a] /= len;
+        double best = -1e300;
+        for (int q = 1; q < NQ; ++q) {
+            double d = nrm[0] * cx(q) + nrm[1] * cy(q) + nrm[2] * cz(q);
+            if (d > best) {
+                best = d;
+                qn = q;
+            }
+        }
+        for (int kk = 1; kk <= 3; ++kk) {
+            int xx = wrap_i(x + kk * cx(qn), g.nx), yy = wrap_i(y + kk * cy(qn), g.ny),
+                zz = z + kk * cz(qn);
+            if (g.bc_z) {
+                if (zz < 0 || zz >= g.nz) break;
+            } else {
+                zz = wrap_i(zz, g.nz);
+            }
+            if (cell_owner(g, so, cp.np, xx, yy, zz) || cell_owner(g, sn, cp.np, xx, yy, zz))
+                break;
+            nbx[m] = xx;
+            nby[m] = yy;
+            nbz[m] = zz;
+            ++m;
+        }
+    }
+    if (m > 0) {
+        C f1[NQ];
+        mem_pull(srcB, g, cp, so, cp.np, nbx[0], nby[0], nbz[0], lin(g, nbx[0], nby[0], nbz[0]),
+                 f1, (Slots*)nullptr, status);
+        if (m == 1) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) fn[q] = f1[q];
+        } else {
+            C f2[NQ];
+            mem_pull(srcB, g, cp, so, cp.np, nbx[1], nby[1], nbz[1],
+                     lin(g, nbx[1], nby[1], nbz[1]), f2, (Slots*)nullptr, status);
+            if (m == 2) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) fn[q] = (C)2 * f1[q] - f2[q];
+            } else {
+                C f3[NQ];
+                mem_pull(srcB, g, cp, so, cp.np, nbx[2], nby[2], nbz[2],
+                         lin(g, nbx[2], nby[2], nbz[2]), f3, (Slots*)nullptr, status);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) fn[q] = (C)3 * f1[q] - (C)3 * f2[q] + f3[q];
+            }
+        }
+        // velocity constraint: only the momentum moment changes (sum_q c_qa^2 = 10)
+        double j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            j[0] += (double)fn[q] * cx(q);
+            j[1] += (double)fn[q] * cy(q);
+            j[2] += (double)fn[q] * cz(q);
+        }
+        double dj[3];
+        for (int a = 0; a < 3; ++a) dj[a] = cp.rho0 * v[a] - j[a];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            fn[q] = (C)((double)fn[q] + (cx(q) * dj[0] + cy(q) * dj[1] + cz(q) * dj[2]) / 10.0);
+    } else {
+        double rbar = cp.rho0;
+        if (extrapolate) {
+            double sum = 0.0;
+            int cnt = 0;
+            for (int q = 1; q < NQ; ++q) {
+                int xx = wrap_i(x + cx(q), g.nx), yy = wrap_i(y + cy(q), g.ny), zz = z + cz(q);
+                if (g.bc_z) {
+                    if (zz < 0 || zz >= g.nz) continue;
+                } else {
+                    zz = wrap_i(zz, g.nz);
+                }
+                if (cell_owner(g, so, cp.np, xx, yy, zz) || cell_owner(g, sn, cp.np, xx, yy, zz))
+                    continue;
+                C fq[NQ];
+                mem_pull(srcB, g, cp, so, cp.np, xx, yy, zz, lin(g, xx, yy, zz), fq,
+                         (Slots*)nullptr, status);
+                double r = 0.0;
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) r += (double)fq[qq];
+                sum += r;
+                ++cnt;
+            }
+            if (cnt > 0) rbar = sum / cnt;
+        }
+        equilibrium((C)rbar, (C)v[0], (C)v[1], (C)v[2], k.rho0, fn);
+    }
+    collide_fluid(fn, k);
+    store_own(dst, g, lin(g, x, y, z), fn);
+}
+
+// ---------------------------------------------------------------------------
+// macroscopic fields of the pre-collision state at the start of the next step
+// what: 2 rho, 3 u, 4 eps (PSM), 5 owner flag (MEM)
+template <typename T, typename C, bool NOSTREAM>
+__global__ void __launch_bounds__(256)
+    k_macro(const T* __restrict__ state, Geom g, Coll<C> k, Coupl cp,
+            const DevParticle* __restrict__ parts, double fx, double fy, double fz, int what,
+            void* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+    const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
+    double* od = reinterpret_cast<double*>(out);
+    if (cp.kind == 2) {
+        int own = cell_owner(g, parts, cp.np, x, y, z);
+        if (what == 5) {
+            reinterpret_cast<int*>(out)[i] = own;
+            return;
+        }
+        if (what == 4) {
+            od[i] = own ? 1.0 : 0.0;
+            return;
+        }
+        double rho, u[3];
+        if (own) {
+            rho = cp.rho0;
+            body_velocity(g, parts[own - 1], xc, yc, zc, u[0], u[1], u[2]);
+        } else {
+            // post-collision moments: rho is conserved, j gains f_ext
+            double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+            for (int q = 0; q < NQ; ++q) {
+                double v = ld(state + (long long)q * g.n + i);
+                r += v;
+                j[0] += v * cx(q);
+                j[1] += v * cy(q);
+                j[2] += v * cz(q);
+            }
+            rho = r;
+            u[0] = (j[0] - fx) / cp.rho0 + fx / (2.0 * cp.rho0);
+            u[1] = (j[1] - fy) / cp.rho0 + fy / (2.0 * cp.rho0);
+            u[2] = (j[2] - fz) / cp.rho0 + fz / (2.0 * cp.rho0);
+        }
+        if (what == 2) od[i] = rho;
+        else {
+            od[3 * i + 0] = u[0];
+            od[3 * i + 1] = u[1];
+            od[3 * i + 2] = u[2];
+        }
+        return;
+    }
+    if (what == 5) {
+        reinterpret_cast<int*>(out)[i] = 0;
+        return;
+    }
+    double B = 0.0, vs[3] = {0.0, 0.0, 0.0}, epsum = 0.0;
+    if (cp.kind == 1) {
+        for (int s = 0; s < cp.np; ++s) {
+            if (!cell_in_reg(g, parts[s].reg, x, y, z)) continue;
+            double e = solid_fraction(g, parts[s], x, y, z, cp.subsample);
+            if (e <= 0.0) continue;
+            epsum += e;
+            double Bs = cp.variant == 0 ? e : e * (cp.tau - 0.5) / ((1.0 - e) + (cp.tau - 0.5));
+            double v[3];
+            body_velocity(g, parts[s], xc, yc, zc, v[0], v[1], v[2]);
+            B += Bs;
+            for (int a = 0; a < 3; ++a) vs[a] += Bs * v[a];
+        }
+    }
+    if (what == 4) {
+        od[i] = epsum;
+        return;
+    }
+    C f[NQ];
+    if (NOSTREAM)
+        load_own(state, g, i, f);
+    else
+        pull_plain(state, g, x, y, z, i, f);
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        r += (double)f[q];
+        j[0] += (double)f[q] * cx(q);
+        j[1] += (double)f[q] * cy(q);
+        j[2] += (double)f[q] * cz(q);
+    }
+    if (what == 2) {
+        od[i] = r;
+        return;
+    }
+    const double fe[3] = {fx, fy, fz};
+    for (int a = 0; a < 3; ++a) {
+        double ua = j[a] / cp.rho0 + fe[a] / (2.0 * cp.rho0);
+        od[3 * i + a] = (1.0 - B) * ua + vs[a];
+    }
+}
+
+template <typename T>
+__global__ void k_init_eq(T* __restrict__ dst, Geom g, double rho, double ux, double uy, double uz,
+                         double rho0) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    double e[NQ];
+    equilibrium(rho, ux, uy, uz, rho0, e);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + i] = (T)e[q];
+}
+
+template <typename T>
+__global__ void k_from_f64(const double* __restrict__ in, T* __restrict__ out, long long count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (T)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+namespace {
+template <typename T, typename C>
+const Coll<C>& coll_of(const Launch& L);
+template <>
+const Coll<double>& coll_of<double, double>(const Launch& L) {
+    return L.kd;
+}
+template <>
+const Coll<float>& coll_of<float, float>(const Launch& L) {
+    return L.kf;
+}
+
+template <typename T>
+cudaError_t bulk_t(const void* src, void* dst, const Launch& L) {
+    dim3 grid(L.g.ntx, L.g.nty, L.g.ntz);
+    const auto& k = coll_of<T, T>(L);
+    if (L.nostream)
+        k_bulk<T, T, true><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k, L.parts,
+                                                           L.cp.np, L.all_tiles);
+    else
+        k_bulk<T, T, false><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
+                                                            L.parts, L.cp.np, L.all_tiles);
+    return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+cudaError_t near_kind(const void* src, void* dst, const Launch& L) {
+    dim3 grid(L.box[0], L.box[1], L.box[2] * L.cp.np);
+    const auto& k = coll_of<T, T>(L);
+    if (L.nostream)
+        k_near<T, T, KIND, true><<<grid, L.block, 0, L.stream>>>(
+            (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, L.partials, L.status, L.box[2]);
+    else
+        k_near<T, T, KIND, false><<<grid, L.block, 0, L.stream>>>(
+            (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, L.partials, L.status, L.box[2]);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t near_t(const void* src, void* dst, const Launch& L) {
+    if (L.cp.np <= 0) return cudaSuccess;
+    if (L.cp.kind == 1) return near_kind<T, 1>(src, dst, L);
+    if (L.cp.kind == 2) return near_kind<T, 2>(src, dst, L);
+    return near_kind<T, 0>(src, dst, L);
+}
+
+template <typename T>
+cudaError_t refill_t(const void* srcB, void* dst, const Launch& L, const DevParticle* po,
+                     const DevParticle* pn, int extrapolate) {
+    if (L.cp.np <= 0) return cudaSuccess;
+    int side = L.box[0];  // set by the caller: cube side in cells
+    long long cells = (long long)side * side * side;
+    dim3 grid((unsigned)((cells + 127) / 128), L.cp.np, 1);
+    k_refill<T, T><<<grid, 128, 0, L.stream>>>((const T*)srcB, (T*)dst, L.g, coll_of<T, T>(L),
+                                                L.cp, po, pn, extrapolate, side, L.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t macro_t(const void* state, const Launch& L, int what, void* out) {
+    unsigned blocks = (unsigned)((L.g.n + 255) / 256);
+    const auto& k = coll_of<T, T>(L);
+    double fx = (double)k.fx, fy = (double)k.fy, fz = (double)k.fz;
+    if (sizeof(T) == 8) {
+        fx = L.kd.fx;
+        fy = L.kd.fy;
+        fz = L.kd.fz;
+    }
+    if (L.nostream)
+        k_macro<T, T, true><<<blocks, 256, 0, L.stream>>>((const T*)state, L.g, k, L.cp, L.parts,
+                                                          fx, fy, fz, what, out);
+    else
+        k_macro<T, T, false><<<blocks, 256, 0, L.stream>>>((const T*)state, L.g, k, L.cp, L.parts,
+                                                           fx, fy, fz, what, out);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_bulk(int storage, const void* src, void* dst, const Launch& L) {
+    return storage == 0 ? bulk_t<double>(src, dst, L) : bulk_t<float>(src, dst, L);
+}
+cudaError_t launch_near(int storage, const void* src, void* dst, const Launch& L) {
+    return storage == 0 ? near_t<double>(src, dst, L) : near_t<float>(src, dst, L);
+}
+cudaError_t launch_refill(int storage, const void* srcB, void* dst, const Launch& L,
+                          const DevParticle* p_old, const DevParticle* p_new, int extrapolate) {
+    return storage == 0 ? refill_t<double>(srcB, dst, L, p_old, p_new, extrapolate)
+                        : refill_t<float>(srcB, dst, L, p_old, p_new, extrapolate);
+}
+cudaError_t launch_macro(int storage, const void* state, const Launch& L, int what, void* out) {
+    return storage == 0 ? macro_t<double>(state, L, what, out) : macro_t<float>(state, L, what, out);
+}
+cudaError_t launch_init_eq(int storage, void* dst, const Launch& L, double rho, double ux,
+                           double uy, double uz) {
+    unsigned blocks = (unsigned)((L.g.n + 255) / 256);
+    if (storage == 0)
+        k_init_eq<double><<<blocks, 256, 0, L.stream>>>((double*)dst, L.g, rho, ux, uy, uz,
+                                                        L.kd.rho0);
+    else
+        k_init_eq<float><<<blocks, 256, 0, L.stream>>>((float*)dst, L.g, rho, ux, uy, uz,
+                                                       L.kd.rho0);
+    return cudaGetLastError();
+}
+cudaError_t launch_from_f64(int storage, const double* in, void* dst, long long count,
+                            cudaStream_t s) {
+    unsigned blocks = (unsigned)((count + 255) / 256);
+    if (storage == 0)
+        return cudaMemcpyAsync(dst, in, sizeof(double) * count, cudaMemcpyDeviceToDevice, s);
+    k_from_f64<float><<<blocks, 256, 0, s>>>(in, (float*)dst, count);
+    return cudaGetLastError();
+}
+cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out) {
+    if (L.cp.np <= 0) return cudaSuccess;
+    k_finalize<<<L.cp.np, 256, 0, L.stream>>>(L.g, L.parts, L.cp.np, L.partials, nsub, force_out);
+    return cudaGetLastError();
+}
+cudaError_t launch_rigid_body(const Launch& L, const double* force, double gx, double gy,
+                              double gz, double dt, int wall_contact) {
+    if (L.cp.np <= 0) return cudaSuccess;
+    k_rigid<<<1, 32, 0, L.stream>>>(L.g, L.parts, L.parts_prev, L.cp.np, force, L.kd.rho0, gx, gy,
+                                    gz, dt, wall_contact, L.status);
+    return cudaGetLastError();
+}
+cudaError_t launch_regions(const Launch& L) {
+    if (L.cp.np <= 0) return cudaSuccess;
+    k_regions<<<1, 32, 0, L.stream>>>(L.g, L.parts, L.cp.np);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgpu

@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must load and export every function that include/lbm_gb300.h
+declares; the binding's structure layouts and constants must match the
+header.  Nothing here launches a kernel.
+"""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_1702_04910_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm_gb300.h")
+
+
+def header_text():
+    with open(HEADER) as fh:
+        return fh.read()
+
+
+def declared_functions():
+    src = re.sub(r"/\*.*?\*/", "", header_text(), flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    try:
+        build.build()
+    except RuntimeError as e:  # toolkit missing: the build check itself fails elsewhere
+        pytest.skip(str(e))
+    return ct.CDLL(build.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_set_particles", "lbm_step", "lbm_get_forces",
+                     "lbm_get_fields", "lbm_destroy"):
+        assert required in names
+    assert set(names) == set(binding.EXPORTED)
+
+
+def test_library_exports_every_declared_function(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared but not exported"
+
+
+def test_abi_version_without_gpu(lib):
+    lib.lbm_abi_version.restype = ct.c_int
+    assert lib.lbm_abi_version() == 1
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    """Argument validation happens before any CUDA call."""
+    lib.lbm_create.restype = ct.c_int
+    lib.lbm_create.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    assert lib.lbm_create(None, None, None) == binding.LBM_ERR_ARG
+    cfg = binding.make_config((8, 8, 8), tau=0.4)  # tau <= 1/2 is invalid
+    h = ct.c_void_p()
+    assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_ARG
+    cfg = binding.make_config((8, 8, 8), coupling="MEM_MR")
+    assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_UNSUPPORTED
+    cfg = binding.make_config((0, 8, 8))
+    assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_ARG
+    lib.lbm_step.restype = ct.c_int
+    lib.lbm_step.argtypes = [ct.c_void_p, ct.c_int]
+    assert lib.lbm_step(None, 1) == binding.LBM_ERR_ARG
+
+
+def test_struct_layouts_match_header():
+    """Field order and sizes of the two public structs (x86-64 / aarch64 LP64)."""
+    assert ct.sizeof(binding.LbmParticle) == 11 * 8 + 8
+    assert binding.LbmConfig.tau.offset == 24
+    assert binding.LbmConfig.storage.offset == 108 and ct.sizeof(binding.LbmConfig) == 112
+    text = header_text()
+    cfg_block = text[text.index("typedef struct {"):text.index("} lbm_config;")]
+    fields = re.findall(r"\b(?:int|double)\s+([a-z_0-9\[\], ]+);", cfg_block)
+    flat = []
+    for f in fields:
+        for name in f.split(","):
+            flat.append(re.sub(r"\[.*\]", "", name).strip())
+    assert flat == [n for n, _ in binding.LbmConfig._fields_]
+
+
+def test_enum_values_match_header():
+    text = header_text()
+    for name, val in binding.COUPLING.items():
+        assert re.search(rf"LBM_{name}\s*=\s*{val}\b", text), name
+    for st, name in binding.STATUS_NAMES.items():
+        assert re.search(rf"{name}\s*=\s*{st}\b", text), name
