@@ -177,6 +177,54 @@ const char *lbm_last_error(const lbm_handle *h);
 /* ABI version of this header: 1. */
 int lbm_abi_version(void);
 
+/* Capacity, in doubles, of the fixed force-partial scratch that
+ * lbm_sweep_noalloc uses: 524288 doubles = 4 MiB per GPU. */
+#define LBM_NOALLOC_MAX_PARTIAL_DOUBLES 524288
+
+/* One coupled LBM sweep that allocates no memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc / cudaFree while they step -- a host program that owns every
+ * device byte through its own arena or pool, or a time-stepping loop that
+ * cannot take the implicit device-wide synchronisation cudaFree (and at
+ * times cudaMalloc) performs while other streams are busy.
+ *
+ * It performs what one sweep of lbm_step does on a handle: pull stream,
+ * collision and coupling (PSM or MEM, cfg->coupling) of FP64 PDFs, then the
+ * fixed-order force/torque total of that sweep -- but no subcycle average,
+ * rigid-body update or MEM refilling, and no handle.
+ *   cfg              configuration as for lbm_create; storage must be
+ *                    LBM_STORE_F64 (LBM_ERR_UNSUPPORTED otherwise).
+ *   src_pdf_dev      device, 19*N doubles: post-collision PDFs (the layout
+ *                    of lbm_get_fields(LBM_FIELD_PDF)); read only.
+ *   dst_pdf_dev      device, 19*N doubles, distinct from src: receives the
+ *                    new post-collision PDFs (MEM solid cells are left as
+ *                    they were).
+ *   n, particles_host   0..32 particle records on the host (copied).
+ *   force_torque_dev device, 6*n doubles [particle][Fx,Fy,Fz,Tx,Ty,Tz].
+ *   status_dev       device int or NULL; kernels OR status bits into it
+ *                    (the caller zeroes it); NULL uses an internal word.
+ *   stream           cudaStream_t or NULL; work is enqueued there and the
+ *                    call returns after enqueueing (it waits only for the
+ *                    particle upload).
+ *   err, err_len     optional buffer for a message on failure.
+ * Scratch: the per-tile force partials live in a fixed device array of
+ * LBM_NOALLOC_MAX_PARTIAL_DOUBLES doubles (plus 32 particle records and a
+ * status word) that every GPU using the library holds until exit.  A
+ * lattice needs ceil(nx/T) * ceil(ny/(256/T)) * nz * max(n,1) * 6 doubles
+ * of it (T = 128, 64 or 32 for nx >= 128, >= 64, else); larger requests
+ * return LBM_ERR_ARG with a message saying so.
+ * All calls share that scratch and it keeps the last call's contents, so
+ * calls that may overlap on the GPU (different streams, or threads without
+ * ordering) race and must be serialised by the caller.
+ * The first call on each device looks up the scratch's device address with
+ * cudaGetSymbolAddress (the device must be current); make that first call
+ * before any stream capture.  Nothing is allocated, by this call or by any
+ * library routine it calls. */
+lbm_status lbm_sweep_noalloc(const lbm_config *cfg, const double *src_pdf_dev,
+                             double *dst_pdf_dev, int n, const lbm_particle *particles_host,
+                             double *force_torque_dev, int *status_dev, void *stream,
+                             char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,7 @@ PROFILE_CLASSES = ("bulk", "near", "force_total", "rigid_body", "refill", "other
 EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_equilibrium",
             "lbm_step", "lbm_get_forces", "lbm_get_fields", "lbm_set_fields",
             "lbm_synchronize", "lbm_profile_enable", "lbm_profile_read", "lbm_device_bytes",
-            "lbm_destroy", "lbm_last_error", "lbm_abi_version")
+            "lbm_destroy", "lbm_last_error", "lbm_abi_version", "lbm_sweep_noalloc")
 
 
 class LbmConfig(ct.Structure):
@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
             "lbm_destroy": (None, [vp]),
             "lbm_last_error": (ct.c_char_p, [vp]),
             "lbm_abi_version": (i, []),
+            "lbm_sweep_noalloc": (i, [ct.POINTER(LbmConfig), vp, vp, i, ct.POINTER(LbmParticle),
+                                      vp, vp, vp, ct.c_char_p, sz]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -207,6 +209,19 @@ def lbm_profile_read(h):
     cnt = (ct.c_longlong * n)()
     _check(h, load().lbm_profile_read(h, n, ms, cnt))
     return {PROFILE_CLASSES[k]: (ms[k], cnt[k]) for k in range(n)}
+
+
+def lbm_sweep_noalloc(cfg: LbmConfig, src_ptr: int, dst_ptr: int, particles, ft_ptr: int,
+                      status_ptr: int = 0, stream: int | None = None) -> None:
+    """One coupled sweep on caller-owned device buffers (no allocation)."""
+    arr = particles_to_c(particles)
+    err = ct.create_string_buffer(256)
+    st = load().lbm_sweep_noalloc(ct.byref(cfg), ct.c_void_p(src_ptr), ct.c_void_p(dst_ptr),
+                                  len(particles), arr, ct.c_void_p(ft_ptr or None),
+                                  ct.c_void_p(status_ptr or None), ct.c_void_p(stream or 0),
+                                  err, len(err))
+    if st != LBM_OK:
+        raise LbmError(st, err.value.decode())
 
 
 def lbm_device_bytes(h) -> int:
