@@ -233,11 +233,48 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_value = world * ncell * sweeps_per_step * args.steps / e2e_s / 1e6
 
-    # FP32 storage variant and its force / velocity error against FP64
+    # FP64 storage with the collision of cells away from particles in
+    # float-float or 64-bit fixed-point arithmetic: speed and error against FP64
     variants = {}
-    if not args.no_fp32:
-        for s in sims:
+    for s in sims:
+        s.close()
+    sims = []
+    arith = {"f64ff": "float-float (2 x FP32) collision away from particles, FP64 elsewhere",
+             "f64fx": "64-bit fixed-point (2^-58) collision away from particles, FP64 elsewhere"}
+    for mode in ([] if args.no_fp32 else ["f64fx", "f64ff"]):
+        simsm = build(mode)
+        for _ in range(args.warmup):
+            for s in simsm:
+                s.step(1)
+        msm, profsm = timed(simsm, args.steps, True)
+        vm = world * ncell * sweeps_per_step * args.steps / (msm * 1e-3) / 1e6
+        bm = sum(p["bulk"][0] for p in profsm) / sum(p["bulk"][1] for p in profsm)
+        achm = bytes_per_cell * bulk_cells / (bm * 1e-3) / 1e9
+        for s in simsm:
             s.close()
+        s64, sm = build("f64"), build(mode)
+        for a, b in zip(s64, sm):
+            a.step(args.acc_steps)
+            b.step(args.acc_steps)
+        ferr, verr, perr = {}, {}, {}
+        for c, a, b in zip(args.couplings, s64, sm):
+            Fa, _ = a.forces()
+            Fb, _ = b.forces()
+            pa, pb = a.get_particles()[0], b.get_particles()[0]
+            ferr[c] = float(np.linalg.norm(Fb - Fa) / max(np.linalg.norm(Fa), 1e-300))
+            verr[c] = float(np.linalg.norm(pb["u"] - pa["u"]) / max(np.linalg.norm(pa["u"]), 1e-300))
+            fa, fb = a.pdf(), b.pdf()
+            perr[c] = float(np.max(np.abs(fb - fa)) / np.max(np.abs(fa)))
+        variants[mode] = {"value": vm, "unit": "MLUPS", "ms_per_step": msm / args.steps,
+                          "bulk_GBps": achm, "frac": achm / peak, "bulk_avg_launch_ms": bm,
+                          "arithmetic": arith[mode], "pdf_max_rel_err_vs_f64": perr,
+                          "force_rel_err_vs_f64": ferr, "particle_velocity_rel_err_vs_f64": verr,
+                          "after_steps": args.acc_steps}
+        for s in s64 + sm:
+            s.close()
+
+    # FP32 storage variant and its force / velocity error against FP64
+    if not args.no_fp32:
         sims64 = build("f64")
         sims32 = build("f32")
         for _ in range(args.warmup):
@@ -267,9 +304,6 @@ def run_ours(args):
                            "force_rel_err_vs_f64": ferr, "particle_velocity_rel_err_vs_f64": verr,
                            "after_steps": nacc}
         for s in sims64 + sims32:
-            s.close()
-    else:
-        for s in sims:
             s.close()
 
     cpu = None
@@ -421,7 +455,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case-shape", default=None,
                     help="run a single small profiling case of this shape (e.g. 128x128x256)")
-    ap.add_argument("--case-storage", default="f64", choices=("f64", "f32"))
+    ap.add_argument("--case-storage", default="f64", choices=("f64", "f32", "f64ff", "f64fx"))
     args = ap.parse_args()
     args.couplings = tuple(c for c in args.couplings.split(",") if c)
     if args.warmup < 3:

@@ -70,8 +70,25 @@ typedef enum {
 typedef enum { LBM_BGK = 0, LBM_TRT = 1 } lbm_collision;
 
 /* PDF storage and collision arithmetic.  Forces, solid fractions and the
- * rigid-body update are FP64 in every mode. */
-typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1 } lbm_storage;
+ * rigid-body update are FP64 in every mode.
+ *   LBM_STORE_F64     FP64 PDFs, FP64 arithmetic.
+ *   LBM_STORE_F32     FP32 PDFs, FP32 collision arithmetic.
+ *   LBM_STORE_F64_FF  FP64 PDFs; the collision of cells away from particles
+ *                     runs in float-float arithmetic (a value is the sum of
+ *                     two floats, ~48 significant bits, converted from and to
+ *                     FP64 with integer operations); cells near particles
+ *                     use FP64.  Same state layout as LBM_STORE_F64.
+ *   LBM_STORE_F64_FX  FP64 PDFs; the collision of cells away from particles
+ *                     runs in 64-bit fixed point (value = integer * 2^-58:
+ *                     exact sums, products to 2^-58), converted from and to
+ *                     FP64 with integer operations; cells near particles use
+ *                     FP64.  Same state layout as LBM_STORE_F64. */
+typedef enum {
+    LBM_STORE_F64 = 0,
+    LBM_STORE_F32 = 1,
+    LBM_STORE_F64_FF = 2,
+    LBM_STORE_F64_FX = 3
+} lbm_storage;
 
 typedef struct {
     int nx, ny, nz;            /* cells per axis, each >= 1                        */
@@ -159,7 +176,8 @@ lbm_status lbm_synchronize(lbm_handle *h);
  * lbm_profile_enable(h, 1) starts recording (and clears the totals);
  * lbm_profile_read returns, for each kernel class k < n_classes
  * (0 bulk sweep, 1 near-particle sweep, 2 force reduction, 3 rigid-body
- * update, 4 MEM refill, 5 other), the summed milliseconds and launches.
+ * update, 4 MEM refill, 5 other: per-step geometry map and set-up
+ * collisions), the summed milliseconds and launches.
  * Reading synchronises the stream. */
 lbm_status lbm_profile_enable(lbm_handle *h, int enable);
 lbm_status lbm_profile_read(lbm_handle *h, int n_classes, double *ms, long long *launches);
@@ -207,12 +225,15 @@ int lbm_abi_version(void);
  *                    call returns after enqueueing (it waits only for the
  *                    particle upload).
  *   err, err_len     optional buffer for a message on failure.
- * Scratch: the per-tile force partials live in a fixed device array of
- * LBM_NOALLOC_MAX_PARTIAL_DOUBLES doubles (plus 32 particle records and a
- * status word) that every GPU using the library holds until exit.  A
- * lattice needs ceil(nx/T) * ceil(ny/(256/T)) * nz * max(n,1) * 6 doubles
- * of it (T = 128, 64 or 32 for nx >= 128, >= 64, else); larger requests
- * return LBM_ERR_ARG with a message saying so.
+ * Scratch: the force partials of the near-particle blocks live in a fixed
+ * device array of LBM_NOALLOC_MAX_PARTIAL_DOUBLES doubles, next to a
+ * geometry map of 1,048,576 16-bit entries (2 MiB), 32 particle records and
+ * a status word; every GPU using the library holds them until exit.  A call
+ * needs max(n,1)^2 * B * 6 doubles of partials, where B = ceil(E_x/32) *
+ * ceil(E_y/2) * E_z and E_a = min(ceil(D_max) + 6, extent of axis a), and
+ * max(n,1) * E_x * E_y * E_z map entries; a request beyond either capacity
+ * (e.g. more than 13 spheres of D = 24) returns LBM_ERR_ARG with a message
+ * saying so, before any device work is enqueued.
  * All calls share that scratch and it keeps the last call's contents, so
  * calls that may overlap on the GPU (different streams, or threads without
  * ordering) race and must be serialised by the caller.

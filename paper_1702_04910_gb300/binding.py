@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR
 COUPLING = {"PSM_M1B1": 0, "PSM_M2B2": 1, "PSM_M3B2": 2, "MEM_BB": 3, "MEM_CLI": 4,
             "MEM_MR": 5, "NONE": 6}
 COLLISION = {"BGK": 0, "TRT": 1}
-STORAGE = {"f64": 0, "f32": 1}
+STORAGE = {"f64": 0, "f32": 1, "f64ff": 2, "f64fx": 3}
 FIELD_PDF, FIELD_PDF_PRE, FIELD_RHO, FIELD_U, FIELD_EPS, FIELD_FLAG = range(6)
 PROFILE_CLASSES = ("bulk", "near", "force_total", "rigid_body", "refill", "other")
 
@@ -257,7 +257,7 @@ class Simulation:
 
     @property
     def pdf_dtype(self):
-        return np.float64 if self.storage == "f64" else np.float32
+        return np.float32 if self.storage == "f32" else np.float64
 
     def set_particles(self, particles):
         lbm_set_particles(self.h, particles)

@@ -42,7 +42,8 @@ struct lbm_handle {
     cudaStream_t stream;
     int device;
     Geom g;
-    int storage;       // 0 FP64, 1 FP32
+    int storage;       // 0 FP64, 1 FP32 (PDF storage / arithmetic of every kernel but k_bulk)
+    int bulk_mode;     // k_bulk arithmetic: 0 FP64, 1 FP32, 2 float-float, 3 fixed point (FP64 PDFs)
     size_t esize;      // bytes per stored PDF value
     void* buf[2];
     int cur;           // buffer holding the stored state
@@ -57,12 +58,17 @@ struct lbm_handle {
     DevParticle* d_prev;
     DevParticle* d_tmp;
     double* d_force;     // [np][6]
-    double* d_partials;  // [subcycles][np][ntiles][6]
+    double* d_partials;  // [subcycles][np regions][near blocks][np][6]
+    size_t partial_cap;  // doubles allocated in d_partials
+    unsigned short* d_map;  // per-step geometry map [np][region box]
+    size_t map_cap;         // entries allocated in d_map
     int* d_status;
     double* h_stage;     // pinned: status word + np*6 forces
     size_t dev_bytes;
     Coll<double> kd;
     Coll<float> kf;
+    Coll<dfloat> kff;
+    Coll<fx64> kfx;
     // profiling
     int profiling;
     std::vector<EventPair> events;
@@ -121,6 +127,8 @@ Launch base_launch(lbm_handle* h) {
     L.g = h->g;
     L.kd = h->kd;
     L.kf = h->kf;
+    L.kff = h->kff;
+    L.kfx = h->kfx;
     L.cp.kind = h->kind;
     L.cp.variant = h->variant;
     L.cp.np = h->np;
@@ -135,15 +143,9 @@ Launch base_launch(lbm_handle* h) {
     L.all_tiles = 0;
     L.block = dim3(h->g.tx, h->g.ty, 1);
     L.stream = h->stream;
-    // near-kernel tile box: tiles spanned by D + 2 halo + 1 cells, plus slack
-    // for a misaligned start and a ragged last tile
-    const double span = h->maxd + 2.0 * NEAR_HALO + 1.0;
-    const int T[3] = {h->g.tx, h->g.ty, 1};
-    const int nt[3] = {h->g.ntx, h->g.nty, h->g.ntz};
-    for (int a = 0; a < 3; ++a) {
-        int b = (int)std::ceil(span / T[a]) + 2;
-        L.box[a] = std::min(b, nt[a]);
-    }
+    near_grid(h->g, h->maxd, L.box);
+    L.map = h->d_map;
+    region_extent(h->g, h->maxd, L.map_ext);
     return L;
 }
 
@@ -178,16 +180,17 @@ Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) {
     return k;
 }
 
-long long ntiles(const lbm_handle* h) { return (long long)h->g.ntx * h->g.nty * h->g.ntz; }
-
 lbm_status free_particles(lbm_handle* h) {
     cudaFree(h->d_parts);
     cudaFree(h->d_prev);
     cudaFree(h->d_tmp);
     cudaFree(h->d_force);
     cudaFree(h->d_partials);
+    cudaFree(h->d_map);
     h->d_parts = h->d_prev = h->d_tmp = nullptr;
     h->d_force = h->d_partials = nullptr;
+    h->d_map = nullptr;
+    h->map_cap = 0;
     if (h->h_stage) cudaFreeHost(h->h_stage);
     h->h_stage = nullptr;
     return LBM_OK;
@@ -197,16 +200,40 @@ lbm_status alloc_particles(lbm_handle* h, int n) {
     free_particles(h);
     size_t np = (size_t)std::max(n, 1);
     size_t part_bytes = sizeof(DevParticle) * np;
-    size_t partial_bytes = sizeof(double) * 6 * (size_t)h->subcycles * np * (size_t)ntiles(h);
     CK(h, cudaMalloc(&h->d_parts, part_bytes), "cudaMalloc particles");
     CK(h, cudaMalloc(&h->d_prev, part_bytes), "cudaMalloc particles");
     CK(h, cudaMalloc(&h->d_tmp, part_bytes), "cudaMalloc particles");
     CK(h, cudaMalloc(&h->d_force, sizeof(double) * 6 * np), "cudaMalloc forces");
-    CK(h, cudaMalloc(&h->d_partials, partial_bytes), "cudaMalloc force partials");
     CK(h, cudaMemsetAsync(h->d_force, 0, sizeof(double) * 6 * np, h->stream), "memset");
-    CK(h, cudaMemsetAsync(h->d_partials, 0, partial_bytes, h->stream), "memset");
     CK(h, cudaMallocHost(&h->h_stage, sizeof(double) * (6 * np + 1)), "cudaMallocHost");
-    h->dev_bytes += 3 * part_bytes + sizeof(double) * 6 * np + partial_bytes;
+    h->partial_cap = 0;
+    return LBM_OK;
+}
+
+// Force partials for `subcycles` sweeps of the near kernel at the current
+// particle count and largest diameter.
+lbm_status ensure_partials(lbm_handle* h) {
+    int box[3];
+    near_grid(h->g, h->maxd, box);
+    const size_t need = (size_t)h->subcycles * (size_t)near_partial_doubles(box, h->np);
+    const size_t mneed0 = (size_t)map_entries(h->g, h->maxd, h->np);
+    if (need <= h->partial_cap && h->d_partials && mneed0 <= h->map_cap && h->d_map) return LBM_OK;
+    if (h->d_partials) {
+        CK(h, cudaStreamSynchronize(h->stream), "partials sync");
+        cudaFree(h->d_partials);
+        h->d_partials = nullptr;
+    }
+    CK(h, cudaMalloc(&h->d_partials, sizeof(double) * need), "cudaMalloc force partials");
+    CK(h, cudaMemsetAsync(h->d_partials, 0, sizeof(double) * need, h->stream), "memset");
+    h->partial_cap = need;
+    const size_t mneed = (size_t)map_entries(h->g, h->maxd, h->np);
+    if (mneed > h->map_cap || !h->d_map) {
+        if (h->d_map) cudaFree(h->d_map);
+        h->d_map = nullptr;
+        CK(h, cudaMalloc(&h->d_map, sizeof(unsigned short) * mneed), "cudaMalloc geometry map");
+        CK(h, cudaMemsetAsync(h->d_map, 0, sizeof(unsigned short) * mneed, h->stream), "memset");
+        h->map_cap = mneed;
+    }
     return LBM_OK;
 }
 
@@ -233,11 +260,11 @@ lbm_status after_pre_state(lbm_handle* h) {
 lbm_status sweep(lbm_handle* h, int sub) {
     Launch L = base_launch(h);
     L.nostream = h->pending_pre;
-    L.partials = h->d_partials + (size_t)sub * (size_t)std::max(h->np, 1) * ntiles(h) * 6;
+    L.partials = h->d_partials + (size_t)sub * (size_t)near_partial_doubles(L.box, h->np);
     const void* src = h->buf[h->cur];
     void* dst = h->buf[1 - h->cur];
     int pi = prof_begin(h, PC_BULK);
-    CK(h, launch_bulk(h->storage, src, dst, L), "bulk sweep launch");
+    CK(h, launch_bulk(h->bulk_mode, src, dst, L), "bulk sweep launch");
     prof_end(h, pi);
     if (h->np > 0) {
         pi = prof_begin(h, PC_NEAR);
@@ -253,6 +280,13 @@ lbm_status step_once(lbm_handle* h) {
     lbm_status st;
     const int coupled = h->np > 0 && h->kind != 0;
     const int nsub = h->kind == 2 ? h->subcycles : 1;
+    if (coupled) {
+        // geometry of the current particle state, shared by the step's sweeps
+        Launch L = base_launch(h);
+        int pi = prof_begin(h, PC_OTHER);
+        CK(h, launch_map(L), "geometry map launch");
+        prof_end(h, pi);
+    }
     for (int s = 0; s < nsub; ++s)
         if ((st = sweep(h, s)) != LBM_OK) return st;
     if (!coupled) return LBM_OK;
@@ -267,7 +301,7 @@ lbm_status step_once(lbm_handle* h) {
     prof_end(h, pi);
     if (h->kind == 2) {
         // re-map with the new state; rebuild uncovered cells (src of the last sweep)
-        L.box[0] = (int)std::ceil(h->maxd) + 4;
+        L.box[0] = (int)std::ceil(h->maxd) + 4;  // refill: cube side in cells
         pi = prof_begin(h, PC_REFILL);
         CK(h, launch_refill(h->storage, h->buf[1 - h->cur], h->buf[h->cur], L, h->d_prev,
                             h->d_parts, 1),
@@ -304,7 +338,12 @@ const char* lbm_last_error(const lbm_handle* h) {
     return h ? h->err : "no handle";
 }
 
-size_t lbm_device_bytes(const lbm_handle* h) { return h ? h->dev_bytes : 0; }
+size_t lbm_device_bytes(const lbm_handle* h) {
+    if (!h) return 0;
+    const size_t np = (size_t)std::max(h->np, 1);
+    return h->dev_bytes + 3 * sizeof(DevParticle) * np + sizeof(double) * 6 * np +
+           sizeof(double) * h->partial_cap + sizeof(unsigned short) * h->map_cap;
+}
 
 lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     if (!cfg || !out) return LBM_ERR_ARG;
@@ -313,9 +352,11 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     if (!(cfg->tau > 0.5) || !(cfg->rho0 > 0.0) || !std::isfinite(cfg->tau)) return LBM_ERR_ARG;
     if (cfg->coupling < 0 || cfg->coupling > LBM_NONE) return LBM_ERR_ARG;
     if (cfg->collision != LBM_BGK && cfg->collision != LBM_TRT) return LBM_ERR_ARG;
-    if (cfg->storage != LBM_STORE_F64 && cfg->storage != LBM_STORE_F32) return LBM_ERR_ARG;
+    if (cfg->storage != LBM_STORE_F64 && cfg->storage != LBM_STORE_F32 &&
+        cfg->storage != LBM_STORE_F64_FF && cfg->storage != LBM_STORE_F64_FX)
+        return LBM_ERR_ARG;
     if (cfg->bc_z != 0 && cfg->bc_z != 1) return LBM_ERR_ARG;
-    if (cfg->subsample < 0 || cfg->subsample > 64 || cfg->lbm_subcycles < 0) return LBM_ERR_ARG;
+    if (cfg->subsample < 0 || cfg->subsample > 40 || cfg->lbm_subcycles < 0) return LBM_ERR_ARG;
     if (cfg->coupling == LBM_MEM_MR) return LBM_ERR_UNSUPPORTED;
     if (cfg->collision == LBM_TRT) {
         double lp = -1.0 / cfg->tau;
@@ -333,7 +374,11 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     if (h->cfg.subsample == 0) h->cfg.subsample = 4;
     h->stream = (cudaStream_t)stream;
     cudaGetDevice(&h->device);
-    h->storage = cfg->storage == LBM_STORE_F64 ? 0 : 1;
+    h->storage = cfg->storage == LBM_STORE_F32 ? 1 : 0;
+    h->bulk_mode = cfg->storage == LBM_STORE_F32      ? 1
+                   : cfg->storage == LBM_STORE_F64_FF ? 2
+                   : cfg->storage == LBM_STORE_F64_FX ? 3
+                                                      : 0;
     h->esize = h->storage == 0 ? sizeof(double) : sizeof(float);
     h->kind = is_psm(cfg->coupling) ? 1 : (is_mem(cfg->coupling) ? 2 : 0);
     h->variant = h->kind == 1 ? cfg->coupling - LBM_PSM_M1B1
@@ -357,6 +402,8 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     const double lm = cfg->collision == LBM_TRT ? 1.0 / (cfg->magic / (0.5 + 1.0 / lp) - 0.5) : lp;
     h->kd = make_coll<double>(lp, lm, cfg->rho0, cfg->force_density);
     h->kf = make_coll<float>(lp, lm, cfg->rho0, cfg->force_density);
+    h->kff = make_coll<dfloat>(lp, lm, cfg->rho0, cfg->force_density);
+    h->kfx = make_coll<fx64>(lp, lm, cfg->rho0, cfg->force_density);
 
     size_t bytes = (size_t)NQ * (size_t)n * h->esize;
     cudaError_t e = cudaMalloc(&h->buf[0], bytes);
@@ -370,6 +417,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     h->dev_bytes = 2 * bytes + sizeof(int);
     cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
     lbm_status st = alloc_particles(h, 0);
+    if (st == LBM_OK) st = ensure_partials(h);
     if (st == LBM_OK) {
         const double u0[3] = {0.0, 0.0, 0.0};
         st = lbm_init_equilibrium(h, cfg->rho0, u0);
@@ -448,6 +496,10 @@ lbm_status lbm_set_particles(lbm_handle* h, int n, const lbm_particle* host_in) 
         if (st != LBM_OK) return st;
     }
     h->maxd = std::max(h->maxd, maxd);
+    {
+        lbm_status st = ensure_partials(h);
+        if (st != LBM_OK) return st;
+    }
     if (remap)
         CK(h, cudaMemcpyAsync(h->d_tmp, h->d_parts, sizeof(DevParticle) * n,
                               cudaMemcpyDeviceToDevice, h->stream),

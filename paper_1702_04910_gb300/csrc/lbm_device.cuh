@@ -206,8 +206,14 @@ __device__ inline AxisRange axis_range(double X, double R, int ncell, int T, int
     return r;
 }
 
+// Offset of index i (in [0, n)) from the wrapped range start lo (in [0, n)).
+__device__ __forceinline__ int range_off(int i, int lo, int n) {
+    const int d = i - lo;
+    return d < 0 ? d + n : d;
+}
+
 __device__ __forceinline__ bool in_range(int i, int lo, int len, int n) {
-    return wrap_i(i - lo, n) < len;
+    return range_off(i, lo, n) < len;
 }
 
 struct NearRegion {
@@ -470,31 +476,72 @@ __device__ __forceinline__ void equilibrium(C rho, C vx, C vy, C vz, C rho0, C (
 }
 
 // ---- PSM solid fraction: n^3 supersampling (Sec. 2.3) -----------------------
-// Cells wholly inside the sphere give 1 and cells whose box misses the sphere
-// give 0 without sampling; both short-cuts agree exactly with the sampled
-// count (samples lie at least 1/(2n) inside the cell, far beyond rounding).
-__device__ inline double solid_fraction(const Geom& g, const DevParticle& P, int x, int y, int z,
-                                        int n) {
+// Number of the n^3 sub-cell samples at ((i + 1/2)/n, ...) inside the sphere.
+// Cells wholly inside the sphere give n^3 and cells whose box misses the
+// sphere give 0 without sampling; both short-cuts agree exactly with the
+// sampled count (samples lie at least 1/(2n) inside the cell, far beyond
+// rounding).  For n a power of two the sample offsets (2i+1) * (1/(2n)) are
+// the same doubles as (i + 1/2)/n, without a division.
+__device__ inline int solid_count(const Geom& g, const DevParticle& P, int x, int y, int z,
+                                  int n) {
     double dx, dy, dz;
     separation(g, x + 0.5, y + 0.5, z + 0.5, P, dx, dy, dz);
     double ax = fabs(dx), ay = fabs(dy), az = fabs(dz);
     double nxd = fmax(ax - 0.5, 0.0), nyd = fmax(ay - 0.5, 0.0), nzd = fmax(az - 0.5, 0.0);
     double R2 = mul_rn(P.r, P.r);
-    if (norm2_rn(nxd, nyd, nzd) > R2 * (1.0 + 1e-12) + 1e-9) return 0.0;
+    if (norm2_rn(nxd, nyd, nzd) > R2 * (1.0 + 1e-12) + 1e-9) return 0;
     double fxd = ax + 0.5, fyd = ay + 0.5, fzd = az + 0.5;
-    if (norm2_rn(fxd, fyd, fzd) < R2 * (1.0 - 1e-12) - 1e-9) return 1.0;
+    if (norm2_rn(fxd, fyd, fzd) < R2 * (1.0 - 1e-12) - 1e-9) return n * n * n;
+    const bool pow2 = (n & (n - 1)) == 0;
+    const double h = 0.5 / n;  // exact for n a power of two
+    const double X = x, Y = y, Z = z;
     int inside = 0;
     for (int k = 0; k < n; ++k) {
-        double pz = z + (k + 0.5) / n;
+        const double pz = Z + (pow2 ? (2 * k + 1) * h : (k + 0.5) / n);
         for (int j = 0; j < n; ++j) {
-            double py = y + (j + 0.5) / n;
+            const double py = Y + (pow2 ? (2 * j + 1) * h : (j + 0.5) / n);
             for (int i = 0; i < n; ++i) {
-                double px = x + (i + 0.5) / n;
+                const double px = X + (pow2 ? (2 * i + 1) * h : (i + 0.5) / n);
                 inside += point_inside(g, P, px, py, pz) ? 1 : 0;
             }
         }
     }
-    return (double)inside / ((double)n * n * n);
+    return inside;
+}
+
+__device__ inline double solid_fraction(const Geom& g, const DevParticle& P, int x, int y, int z,
+                                        int n) {
+    return (double)solid_count(g, P, x, y, z, n) / ((double)n * n * n);
+}
+
+// Per-step geometry map of a particle's near region (see k_map): MEM owner
+// (0 fluid, s+1 inside particle s) or PSM supersample count of that particle.
+struct GeoMap {
+    const unsigned short* map;  // [particle][z][y][x] over the region box
+    int ex, ey, ez;             // box extents (cells)
+};
+
+// Region offsets of (x,y,z) in particle s's region; false if outside it.
+__device__ __forceinline__ bool region_offsets(const Geom& g, const int* r, int x, int y, int z,
+                                               int& ox, int& oy, int& oz) {
+    ox = range_off(x, r[0], g.nx);
+    oy = range_off(y, r[4], g.ny);
+    oz = range_off(z, r[8], g.nz);
+    return ox < r[1] && oy < r[5] && oz < r[9];
+}
+
+__device__ __forceinline__ unsigned short map_at(const GeoMap& m, int s, int ox, int oy, int oz) {
+    return __ldg(m.map + (((long long)s * m.ez + oz) * m.ey + oy) * m.ex + ox);
+}
+
+// MEM owner of a cell from the map (0 fluid, s+1 inside particle s).
+__device__ __forceinline__ int mapped_owner(const Geom& g, const DevParticle* parts, int np,
+                                            const GeoMap& m, int x, int y, int z) {
+    for (int s = 0; s < np; ++s) {
+        int ox, oy, oz;
+        if (region_offsets(g, parts[s].reg, x, y, z, ox, oy, oz)) return map_at(m, s, ox, oy, oz);
+    }
+    return 0;
 }
 
 // ---- MEM link geometry ---------------------------------------------------------

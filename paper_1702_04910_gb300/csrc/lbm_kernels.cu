@@ -2,14 +2,14 @@
 //
 // One global step (Algorithm 1 / Algorithm 2 of Rettinger & Ruede,
 // arXiv:1702.04910) is built from:
-//   k_bulk      fused pull stream + fluid collision for every tile that no
+//   k_bulk      fused pull stream + fluid collision for every cell that no
 //               particle comes near (the whole domain but an O(D^3) box);
-//   k_near      the same for the tiles near a particle, with the coupling:
+//   k_near      the same for the cells near a particle, with the coupling:
 //               PSM solid fractions and weighted collision Eq. (20)-(26) and
 //               force/torque Eq. (28)-(29), or MEM link boundary conditions
-//               Eq. (12)/(14) and link forces Eq. (16); per-tile force
+//               Eq. (12)/(14) and link forces Eq. (16); per-block force
 //               partials reduced warp -> block in a fixed order;
-//   k_finalize  fixed-order sum of the tile partials, subcycle average;
+//   k_finalize  fixed-order sum of the block partials, subcycle average;
 //   k_rigid     explicit Euler rigid-body update;
 //   k_refill    MEM re-mapping: PDF reconstruction Eq. (19) of uncovered
 //               cells, then their collision.
@@ -74,11 +74,19 @@ __device__ __forceinline__ void cross3(const double (&a)[3], const double (&b)[3
 // In pull form the link of the paper (fluid x, solid neighbour x + c_qp)
 // appears while filling direction q = qbar_p: the upstream cell x - c_q is
 // x + c_qp.
+// Owner of a cell: from the per-step map when given, else evaluated from the
+// particle records (same predicate, R6).
+__device__ __forceinline__ int owner_of(const Geom& g, const DevParticle* parts, int np,
+                                        const GeoMap* gm, int x, int y, int z) {
+    return gm ? mapped_owner(g, parts, np, *gm, x, y, z) : cell_owner(g, parts, np, x, y, z);
+}
+
 template <typename T, typename C, int Q>
 __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Geom& g,
                                              const Coupl& cp, const DevParticle* parts, int np,
-                                             const Nbr& b, int x, int y, int z, long long idx,
-                                             C (&f)[NQ], Slots* slots, int* status) {
+                                             const GeoMap* gm, const Nbr& b, int x, int y, int z,
+                                             long long idx, C (&f)[NQ], Slots* slots,
+                                             int* status) {
     constexpr int QP = opp(Q);  // paper's link direction (towards the solid cell)
     int xs, ys, zs;
     shifted<Q>(b, x, y, z, -1, xs, ys, zs);
@@ -86,14 +94,7 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
         f[Q] = (C)__ldg(src + (long long)QP * g.n + idx);
         return;
     }
-    int owner = 0;
-    for (int s = 0; s < np; ++s) {
-        if (!cell_in_reg(g, parts[s].reg, x, y, z)) continue;
-        if (cell_inside(g, parts[s], xs, ys, zs)) {
-            owner = s + 1;
-            break;
-        }
-    }
+    const int owner = owner_of(g, parts, np, gm, xs, ys, zs);
     if (!owner) {
         f[Q] = (C)__ldg(src + (long long)Q * g.n + lin(g, xs, ys, zs));
         return;
@@ -115,15 +116,7 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
         int x2, y2, z2;
         shifted<Q>(b, x, y, z, +1, x2, y2, z2);
         bool ok = !(cz(Q) != 0 && (z2 < 0 || z2 >= g.nz));
-        if (ok) {
-            for (int s = 0; s < np; ++s) {
-                if (!cell_in_reg(g, parts[s].reg, x, y, z)) continue;
-                if (cell_inside(g, parts[s], x2, y2, z2)) {
-                    ok = false;
-                    break;
-                }
-            }
-        }
+        if (ok) ok = owner_of(g, parts, np, gm, x2, y2, z2) == 0;
         if (ok) {
             const double k0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
             const double alpha = 4.0 / (1.0 + 2.0 * delta);
@@ -150,26 +143,28 @@ template <typename T, typename C, int Q>
 struct MemPull {
     __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
                                                const Coupl& cp, const DevParticle* parts, int np,
-                                               const Nbr& b, int x, int y, int z, long long idx,
-                                               C (&f)[NQ], Slots* slots, int* status) {
-        mem_pull_one<T, C, Q>(src, g, cp, parts, np, b, x, y, z, idx, f, slots, status);
-        MemPull<T, C, Q + 1>::run(src, g, cp, parts, np, b, x, y, z, idx, f, slots, status);
+                                               const GeoMap* gm, const Nbr& b, int x, int y, int z,
+                                               long long idx, C (&f)[NQ], Slots* slots,
+                                               int* status) {
+        mem_pull_one<T, C, Q>(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status);
+        MemPull<T, C, Q + 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status);
     }
 };
 template <typename T, typename C>
 struct MemPull<T, C, NQ> {
     __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const Coupl&,
-                                               const DevParticle*, int, const Nbr&, int, int, int,
-                                               long long, C (&)[NQ], Slots*, int*) {}
+                                               const DevParticle*, int, const GeoMap*, const Nbr&,
+                                               int, int, int, long long, C (&)[NQ], Slots*, int*) {}
 };
 
 template <typename T, typename C>
 __device__ __forceinline__ void mem_pull(const T* __restrict__ src, const Geom& g, const Coupl& cp,
-                                         const DevParticle* parts, int np, int x, int y, int z,
-                                         long long idx, C (&f)[NQ], Slots* slots, int* status) {
+                                         const DevParticle* parts, int np, const GeoMap* gm,
+                                         int x, int y, int z, long long idx, C (&f)[NQ],
+                                         Slots* slots, int* status) {
     Nbr b = make_nbr(g, x, y, z);
     f[0] = (C)__ldg(src + idx);
-    MemPull<T, C, 1>::run(src, g, cp, parts, np, b, x, y, z, idx, f, slots, status);
+    MemPull<T, C, 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -228,18 +223,24 @@ __device__ inline void psm_collide(C (&f)[NQ], const Coll<C>& k, const Coupl& cp
 }
 
 // ---------------------------------------------------------------------------
-// bulk sweep: tiles no particle comes near
+// bulk sweep: every cell outside the near-particle regions.  Tiles that no
+// region touches skip the per-cell test (block-uniform branch).
 template <typename T, typename C, bool NOSTREAM>
 __global__ void __launch_bounds__(256)
     k_bulk(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k,
            const DevParticle* __restrict__ parts, int np, int all_tiles) {
     const int tX = blockIdx.x, tY = blockIdx.y, tZ = blockIdx.z;
+    bool near_tile = false;
     if (!all_tiles) {
-        for (int s = 0; s < np; ++s)
-            if (tile_in_reg(g, parts[s].reg, tX, tY, tZ)) return;
+        for (int s = 0; s < np && !near_tile; ++s)
+            near_tile = tile_in_reg(g, parts[s].reg, tX, tY, tZ);
     }
     const int x = tX * g.tx + threadIdx.x, y = tY * g.ty + threadIdx.y, z = tZ;
     if (x >= g.nx || y >= g.ny) return;
+    if (near_tile) {
+        for (int s = 0; s < np; ++s)
+            if (cell_in_reg(g, parts[s].reg, x, y, z)) return;  // k_near's cell
+    }
     const long long idx = lin(g, x, y, z);
     C f[NQ];
     if (NOSTREAM)
@@ -251,30 +252,37 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// near-particle sweep.  Grid (box_x, box_y, box_z * np): block (kx, ky, kz)
-// of particle p handles tile (tlo + k) of p's region unless a lower-index
-// particle's region also holds that tile.
+// near-particle sweep over the cell region of each particle (cells within
+// R + NEAR_HALO of the centre per axis).  Grid (bx, by, bz * np) of
+// NEAR_BX x NEAR_BY x NEAR_BZ blocks: block (bx, by, bz) of particle p covers
+// region offsets [bx*NEAR_BX, ...) etc.; a cell that also lies in the region
+// of a lower-index particle is left to that particle's blocks.  Each block
+// writes, for every particle q, its fixed-order force/torque sum to
+// partials[((p * nblk + blk) * np + q) * 6 + c].
 template <typename T, typename C, int KIND, bool NOSTREAM>
 __global__ void __launch_bounds__(256)
     k_near(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
-           const DevParticle* __restrict__ parts, double* __restrict__ partials,
+           const DevParticle* __restrict__ parts, GeoMap gm, double* __restrict__ partials,
            int* __restrict__ status, int bz) {
     __shared__ DevParticle sp[MAX_PARTICLES];
     __shared__ double red[8][6];
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.x + NEAR_BX * (threadIdx.y + NEAR_BY * threadIdx.z);
+    constexpr int nthr = NEAR_BX * NEAR_BY * NEAR_BZ;
     for (int i = tid; i < cp.np * (int)(sizeof(DevParticle) / sizeof(double)); i += nthr)
         reinterpret_cast<double*>(sp)[i] = reinterpret_cast<const double*>(parts)[i];
     __syncthreads();
-    const int p = blockIdx.z / bz, kz = blockIdx.z % bz, kx = blockIdx.x, ky = blockIdx.y;
+    const int p = blockIdx.z / bz, bzz = blockIdx.z % bz;
     const int* R = sp[p].reg;
-    if (kx >= R[3] || ky >= R[7] || kz >= R[11]) return;
-    const int tX = (R[2] + kx) % g.ntx, tY = (R[6] + ky) % g.nty, tZ = (R[10] + kz) % g.ntz;
-    for (int s = 0; s < p; ++s)
-        if (tile_in_reg(g, sp[s].reg, tX, tY, tZ)) return;
-
-    const int x = tX * g.tx + threadIdx.x, y = tY * g.ty + threadIdx.y, z = tZ;
-    const bool active = x < g.nx && y < g.ny;
+    const int kx = blockIdx.x * NEAR_BX + threadIdx.x, ky = blockIdx.y * NEAR_BY + threadIdx.y,
+              kz = bzz * NEAR_BZ + threadIdx.z;
+    bool active = kx < R[1] && ky < R[5] && kz < R[9];
+    int x = R[0] + kx, y = R[4] + ky, z = R[8] + kz;
+    if (x >= g.nx) x -= g.nx;
+    if (y >= g.ny) y -= g.ny;
+    if (z >= g.nz) z -= g.nz;
+    if (active)
+        for (int s = 0; s < p; ++s)
+            if (cell_in_reg(g, sp[s].reg, x, y, z)) active = false;
     Slots slots;
     slots.clear();
     if (active) {
@@ -282,15 +290,12 @@ __global__ void __launch_bounds__(256)
         C f[NQ];
         if (KIND == 2) {
             // MEM: solid cells are not updated (Sec. 2.2)
-            int own = 0;
-            for (int s = 0; s < cp.np && !own; ++s)
-                if (cell_in_reg(g, sp[s].reg, x, y, z) && cell_inside(g, sp[s], x, y, z))
-                    own = s + 1;
+            const int own = map_at(gm, p, kx, ky, kz);
             if (!own) {
                 if (NOSTREAM)
                     load_own(src, g, idx, f);
                 else
-                    mem_pull(src, g, cp, sp, cp.np, x, y, z, idx, f, &slots, status);
+                    mem_pull(src, g, cp, sp, cp.np, &gm, x, y, z, idx, f, &slots, status);
                 collide_fluid(f, k);
                 store_own(dst, g, idx, f);
             }
@@ -303,10 +308,13 @@ __global__ void __launch_bounds__(256)
             int pid[CELL_SLOTS];
             double eps[CELL_SLOTS];
             if (KIND == 1) {
+                const double n3 = (double)cp.subsample * cp.subsample * cp.subsample;
                 for (int s = 0; s < cp.np; ++s) {
-                    if (!cell_in_reg(g, sp[s].reg, x, y, z)) continue;
-                    double e = solid_fraction(g, sp[s], x, y, z, cp.subsample);
-                    if (e <= 0.0) continue;
+                    int ox, oy, oz;
+                    if (!region_offsets(g, sp[s].reg, x, y, z, ox, oy, oz)) continue;
+                    const int cnt = map_at(gm, s, ox, oy, oz);
+                    if (cnt == 0) continue;
+                    const double e = (double)cnt / n3;
                     if (nobj < CELL_SLOTS) {
                         pid[nobj] = s;
                         eps[nobj] = e;
@@ -324,51 +332,72 @@ __global__ void __launch_bounds__(256)
         }
     }
     if (KIND == 0 || (NOSTREAM && KIND == 2)) return;
-    // fixed-order reduction of this tile's contribution for each particle
-    const int ntiles = g.ntx * g.nty * g.ntz;
-    const long long tile = (long long)tX + (long long)g.ntx * ((long long)tY + (long long)g.nty * tZ);
-    const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
-    for (int s = 0; s < cp.np; ++s) {
-        if (!tile_in_reg(g, sp[s].reg, tX, tY, tZ)) continue;
+    // fixed-order reduction of this block's contribution for each particle
+    const long long nblk = (long long)gridDim.x * gridDim.y * bz;
+    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * bzz);
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr / 32;
+    for (int q = 0; q < cp.np; ++q) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            double v = warp_sum(slots.get(s, c));
+            double v = warp_sum(slots.get(q, c));
             if (lane == 0) red[warp][c] = v;
         }
         __syncthreads();
         if (tid < 6) {
             double acc = 0.0;
             for (int w = 0; w < nwarp; ++w) acc += red[w][tid];
-            partials[((long long)s * ntiles + tile) * 6 + tid] = acc;
+            partials[(((long long)p * nblk + blk) * cp.np + q) * 6 + tid] = acc;
         }
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// fixed-order force/torque total of particle p (one block per particle):
-// F = (S_1 + ... + S_nsub) / nsub with S_k the sum of the tile partials of
-// subcycle k over p's region.
+// Per-step geometry map (computed once per global step, before the sweeps):
+// for every cell of particle p's region, MEM: the owner under the current
+// particle state (0 fluid, s+1 inside particle s, lowest s first, R6);
+// PSM: the number of the n^3 supersamples inside particle p (R15).  The
+// sweeps then read these instead of re-evaluating FP64 geometry per link.
+// Grid (ceil(ex/32), ey, ez * np), 32 threads per block.
+template <int KIND>
+__global__ void __launch_bounds__(32)
+    k_map(Geom g, Coupl cp, const DevParticle* __restrict__ parts, unsigned short* __restrict__ map,
+          int ex, int ey, int ez) {
+    __shared__ DevParticle sp[MAX_PARTICLES];
+    const int nd = cp.np * (int)(sizeof(DevParticle) / sizeof(double));
+    for (int i = threadIdx.x; i < nd; i += blockDim.x)
+        reinterpret_cast<double*>(sp)[i] = reinterpret_cast<const double*>(parts)[i];
+    __syncthreads();
+    const int p = blockIdx.z / ez, kz = blockIdx.z % ez, ky = blockIdx.y;
+    const int kx = blockIdx.x * 32 + threadIdx.x;
+    const int* R = sp[p].reg;
+    if (kx >= R[1] || ky >= R[5] || kz >= R[9]) return;
+    int x = R[0] + kx, y = R[4] + ky, z = R[8] + kz;
+    if (x >= g.nx) x -= g.nx;
+    if (y >= g.ny) y -= g.ny;
+    if (z >= g.nz) z -= g.nz;
+    const int v = KIND == 2 ? cell_owner(g, sp, cp.np, x, y, z)
+                            : solid_count(g, sp[p], x, y, z, cp.subsample);
+    map[(((long long)p * ez + kz) * ey + ky) * ex + kx] = (unsigned short)v;
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order force/torque total of particle q (one block per particle):
+// F = (S_1 + ... + S_nsub) / nsub with S_k the sum, over the near-kernel
+// blocks of every particle's region, of subcycle k's partials for q.
 __global__ void __launch_bounds__(256)
-    k_finalize(Geom g, const DevParticle* __restrict__ parts, int np,
-               const double* __restrict__ partials, int nsub, double* __restrict__ out) {
+    k_finalize(int np, long long nblk, const double* __restrict__ partials, int nsub,
+               double* __restrict__ out) {
     __shared__ double red[256][6];
-    const int p = blockIdx.x, tid = threadIdx.x;
-    const int* R = parts[p].reg;
-    const long long count = (long long)R[3] * R[7] * R[11];
-    const int ntiles = g.ntx * g.nty * g.ntz;
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const long long count = (long long)np * nblk;
     double tot[6] = {0, 0, 0, 0, 0, 0};
     for (int sub = 0; sub < nsub; ++sub) {
-        const double* base = partials + ((long long)sub * np + p) * ntiles * 6;
+        const double* base = partials + (long long)sub * count * np * 6;
         double acc[6] = {0, 0, 0, 0, 0, 0};
         for (long long kk = tid; kk < count; kk += blockDim.x) {
-            int kx = (int)(kk % R[3]);
-            int ky = (int)((kk / R[3]) % R[7]);
-            int kz = (int)(kk / ((long long)R[3] * R[7]));
-            int tX = (R[2] + kx) % g.ntx, tY = (R[6] + ky) % g.nty, tZ = (R[10] + kz) % g.ntz;
-            long long tile = (long long)tX + (long long)g.ntx * ((long long)tY + (long long)g.nty * tZ);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) acc[c] += base[tile * 6 + c];
+            for (int c = 0; c < 6; ++c) acc[c] += base[(kk * np + q) * 6 + c];
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) red[tid][c] = acc[c];
@@ -385,7 +414,7 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
     }
     if (tid == 0)
-        for (int c = 0; c < 6; ++c) out[p * 6 + c] = tot[c] / nsub;
+        for (int c = 0; c < 6; ++c) out[q * 6 + c] = tot[c] / nsub;
 }
 
 // ---------------------------------------------------------------------------
@@ -523,21 +552,21 @@ __global__ void __launch_bounds__(128)
     }
     if (m > 0) {
         C f1[NQ];
-        mem_pull(srcB, g, cp, so, cp.np, nbx[0], nby[0], nbz[0], lin(g, nbx[0], nby[0], nbz[0]),
+        mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, nbx[0], nby[0], nbz[0], lin(g, nbx[0], nby[0], nbz[0]),
                  f1, (Slots*)nullptr, status);
         if (m == 1) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) fn[q] = f1[q];
         } else {
             C f2[NQ];
-            mem_pull(srcB, g, cp, so, cp.np, nbx[1], nby[1], nbz[1],
+            mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, nbx[1], nby[1], nbz[1],
                      lin(g, nbx[1], nby[1], nbz[1]), f2, (Slots*)nullptr, status);
             if (m == 2) {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) fn[q] = (C)2 * f1[q] - f2[q];
             } else {
                 C f3[NQ];
-                mem_pull(srcB, g, cp, so, cp.np, nbx[2], nby[2], nbz[2],
+                mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, nbx[2], nby[2], nbz[2],
                          lin(g, nbx[2], nby[2], nbz[2]), f3, (Slots*)nullptr, status);
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) fn[q] = (C)3 * f1[q] - (C)3 * f2[q] + f3[q];
@@ -571,7 +600,7 @@ __global__ void __launch_bounds__(128)
                 if (cell_owner(g, so, cp.np, xx, yy, zz) || cell_owner(g, sn, cp.np, xx, yy, zz))
                     continue;
                 C fq[NQ];
-                mem_pull(srcB, g, cp, so, cp.np, xx, yy, zz, lin(g, xx, yy, zz), fq,
+                mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, xx, yy, zz, lin(g, xx, yy, zz), fq,
                          (Slots*)nullptr, status);
                 double r = 0.0;
 #pragma unroll
@@ -713,16 +742,24 @@ template <>
 const Coll<float>& coll_of<float, float>(const Launch& L) {
     return L.kf;
 }
+template <>
+const Coll<dfloat>& coll_of<double, dfloat>(const Launch& L) {
+    return L.kff;
+}
+template <>
+const Coll<fx64>& coll_of<double, fx64>(const Launch& L) {
+    return L.kfx;
+}
 
-template <typename T>
+template <typename T, typename C = T>
 cudaError_t bulk_t(const void* src, void* dst, const Launch& L) {
     dim3 grid(L.g.ntx, L.g.nty, L.g.ntz);
-    const auto& k = coll_of<T, T>(L);
+    const auto& k = coll_of<T, C>(L);
     if (L.nostream)
-        k_bulk<T, T, true><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k, L.parts,
+        k_bulk<T, C, true><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k, L.parts,
                                                            L.cp.np, L.all_tiles);
     else
-        k_bulk<T, T, false><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
+        k_bulk<T, C, false><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
                                                             L.parts, L.cp.np, L.all_tiles);
     return cudaGetLastError();
 }
@@ -730,13 +767,15 @@ cudaError_t bulk_t(const void* src, void* dst, const Launch& L) {
 template <typename T, int KIND>
 cudaError_t near_kind(const void* src, void* dst, const Launch& L) {
     dim3 grid(L.box[0], L.box[1], L.box[2] * L.cp.np);
+    dim3 block(NEAR_BX, NEAR_BY, NEAR_BZ);
     const auto& k = coll_of<T, T>(L);
+    const GeoMap gm{L.map, L.map_ext[0], L.map_ext[1], L.map_ext[2]};
     if (L.nostream)
-        k_near<T, T, KIND, true><<<grid, L.block, 0, L.stream>>>(
-            (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, L.partials, L.status, L.box[2]);
+        k_near<T, T, KIND, true><<<grid, block, 0, L.stream>>>(
+            (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, gm, L.partials, L.status, L.box[2]);
     else
-        k_near<T, T, KIND, false><<<grid, L.block, 0, L.stream>>>(
-            (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, L.partials, L.status, L.box[2]);
+        k_near<T, T, KIND, false><<<grid, block, 0, L.stream>>>(
+            (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, gm, L.partials, L.status, L.box[2]);
     return cudaGetLastError();
 }
 
@@ -781,6 +820,8 @@ cudaError_t macro_t(const void* state, const Launch& L, int what, void* out) {
 }  // namespace
 
 cudaError_t launch_bulk(int storage, const void* src, void* dst, const Launch& L) {
+    if (storage == 2) return bulk_t<double, dfloat>(src, dst, L);
+    if (storage == 3) return bulk_t<double, fx64>(src, dst, L);
     return storage == 0 ? bulk_t<double>(src, dst, L) : bulk_t<float>(src, dst, L);
 }
 cudaError_t launch_near(int storage, const void* src, void* dst, const Launch& L) {
@@ -813,9 +854,22 @@ cudaError_t launch_from_f64(int storage, const double* in, void* dst, long long 
     k_from_f64<float><<<blocks, 256, 0, s>>>(in, (float*)dst, count);
     return cudaGetLastError();
 }
+cudaError_t launch_map(const Launch& L) {
+    if (L.cp.np <= 0 || L.cp.kind == 0) return cudaSuccess;
+    dim3 grid((L.map_ext[0] + 31) / 32, L.map_ext[1], L.map_ext[2] * L.cp.np);
+    if (L.cp.kind == 2)
+        k_map<2><<<grid, 32, 0, L.stream>>>(L.g, L.cp, L.parts, L.map, L.map_ext[0], L.map_ext[1],
+                                            L.map_ext[2]);
+    else
+        k_map<1><<<grid, 32, 0, L.stream>>>(L.g, L.cp, L.parts, L.map, L.map_ext[0], L.map_ext[1],
+                                            L.map_ext[2]);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out) {
     if (L.cp.np <= 0) return cudaSuccess;
-    k_finalize<<<L.cp.np, 256, 0, L.stream>>>(L.g, L.parts, L.cp.np, L.partials, nsub, force_out);
+    k_finalize<<<L.cp.np, 256, 0, L.stream>>>(L.cp.np, near_blocks(L.box), L.partials, nsub,
+                                               force_out);
     return cudaGetLastError();
 }
 cudaError_t launch_rigid_body(const Launch& L, const double* force, double gx, double gy,

@@ -3,8 +3,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 
 #include "lbm_device.cuh"
+#include "lbm_dfloat.cuh"
+#include "lbm_fixed.cuh"
 
 namespace lbmgpu {
 
@@ -12,6 +15,8 @@ struct Launch {
     Geom g;
     Coll<double> kd;   // FP64 collision constants
     Coll<float> kf;    // FP32 collision constants
+    Coll<dfloat> kff;  // float-float collision constants (FP64 storage)
+    Coll<fx64> kfx;    // fixed-point collision constants (FP64 storage)
     Coupl cp;
     DevParticle* parts;       // particle state used by this sweep
     DevParticle* parts_prev;  // state before the last rigid-body update (refill)
@@ -19,10 +24,46 @@ struct Launch {
     int* status;
     int nostream;             // 1: stored buffer holds pre-collision f (no stream)
     int all_tiles;            // bulk kernel: process every tile (no coupling)
-    int box[3];               // near-kernel tile box per particle
+    int box[3];               // near-kernel grid per particle (blocks per axis)
+    unsigned short* map;      // per-step geometry map (see k_map)
+    int map_ext[3];           // region box extents of the map (cells)
     dim3 block;
     cudaStream_t stream;
 };
+
+// Near-kernel block shape and grid: a particle's cell region spans at most
+// D + 2 NEAR_HALO + 1 cells per axis; the grid covers ceil(D) + 6 cells.
+constexpr int NEAR_BX = 32, NEAR_BY = 2, NEAR_BZ = 1;
+
+// Cells per axis of the region box that holds any particle of diameter <= maxd.
+inline void region_extent(const Geom& g, double maxd, int ext[3]) {
+    const int span = (int)ceil(maxd) + 2 * (int)NEAR_HALO + 2;
+    ext[0] = g.nx < span ? g.nx : span;
+    ext[1] = g.ny < span ? g.ny : span;
+    ext[2] = g.nz < span ? g.nz : span;
+}
+
+inline void near_grid(const Geom& g, double maxd, int box[3]) {
+    int ext[3];
+    region_extent(g, maxd, ext);
+    const int b[3] = {NEAR_BX, NEAR_BY, NEAR_BZ};
+    for (int a = 0; a < 3; ++a) box[a] = (ext[a] + b[a] - 1) / b[a];
+}
+
+// Map entries (unsigned short) for np particles.
+inline long long map_entries(const Geom& g, double maxd, int np) {
+    int ext[3];
+    region_extent(g, maxd, ext);
+    return (long long)(np > 0 ? np : 1) * ext[0] * ext[1] * ext[2];
+}
+
+inline long long near_blocks(const int box[3]) { return (long long)box[0] * box[1] * box[2]; }
+
+// Doubles of force partials one sweep needs: np regions x blocks x np x 6.
+inline long long near_partial_doubles(const int box[3], int np) {
+    const long long n = np > 0 ? np : 1;
+    return n * near_blocks(box) * n * 6;
+}
 
 // Status bits raised by kernels (OR-ed into *status).
 enum : int {
@@ -31,7 +72,9 @@ enum : int {
     ST_REFILL_SOLID = 4,      // refill found no particle owning a cell (internal)
 };
 
-// storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision)
+// storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision);
+// launch_bulk also takes 2 = FP64 storage with float-float collision and
+// 3 = FP64 storage with 64-bit fixed-point collision
 cudaError_t launch_bulk(int storage, const void* src, void* dst, const Launch& L);
 cudaError_t launch_near(int storage, const void* src, void* dst, const Launch& L);
 cudaError_t launch_refill(int storage, const void* srcB, void* dst, const Launch& L,
@@ -43,6 +86,7 @@ cudaError_t launch_from_f64(int storage, const double* in, void* dst, long long 
                             cudaStream_t s);
 cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out);
 cudaError_t launch_regions(const Launch& L);
+cudaError_t launch_map(const Launch& L);
 cudaError_t launch_rigid_body(const Launch& L, const double* force, double gx, double gy,
                               double gz, double dt, int wall_contact);
 

@@ -8,7 +8,7 @@
 // other streams are busy.  The handle-based API allocates its buffers in
 // lbm_create / lbm_set_particles; this entry point instead takes the PDF
 // buffers and the force output from the caller and keeps its only scratch --
-// the per-tile force/torque partials, the particle records and a status
+// the per-block force/torque partials, the particle records and a status
 // word -- in fixed file-scope device arrays below.
 #include <cuda_runtime.h>
 
@@ -25,11 +25,16 @@ using namespace lbmgpu;
 namespace {
 
 // Scratch shared by every call on a device (held by each GPU that loads the
-// library until the process exits).
+// library until the process exits): near-kernel force partials
+// (np regions x blocks x np x 6 doubles, see near_partial_doubles), the
+// per-call geometry map (np x region box entries), the particle records and
+// a status word.
 constexpr size_t NOALLOC_PARTIAL_DOUBLES = LBM_NOALLOC_MAX_PARTIAL_DOUBLES;
 static __device__ __align__(256) double g_partials[NOALLOC_PARTIAL_DOUBLES];
 static __device__ __align__(256) DevParticle g_particles[MAX_PARTICLES];
 static __device__ __align__(256) int g_status[64];
+constexpr size_t NOALLOC_MAP_ENTRIES = 1 << 20;  // geometry map, 2 MiB
+static __device__ __align__(256) unsigned short g_map[NOALLOC_MAP_ENTRIES];
 
 constexpr int MAX_DEVICES = 64;
 struct Addresses {
@@ -37,6 +42,7 @@ struct Addresses {
     double* partials;
     DevParticle* particles;
     int* status;
+    unsigned short* map;
 };
 Addresses g_addr[MAX_DEVICES];
 std::mutex g_addr_mutex;
@@ -54,6 +60,7 @@ cudaError_t scratch_addresses(int dev, Addresses& out) {
         cudaError_t e = cudaGetSymbolAddress((void**)&a.partials, g_partials);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&a.particles, g_particles);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&a.status, g_status);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&a.map, g_map);
         if (e != cudaSuccess) return e;
         a.ready = true;
     }
@@ -106,18 +113,6 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     g.ntx = (cfg->nx + g.tx - 1) / g.tx;
     g.nty = (cfg->ny + g.ty - 1) / g.ty;
     g.ntz = cfg->nz;
-    const long long ntiles = (long long)g.ntx * g.nty * g.ntz;
-    if ((unsigned long long)ntiles * (unsigned long long)std::max(n, 1) * 6ULL >
-        (unsigned long long)NOALLOC_PARTIAL_DOUBLES) {
-        char msg[200];
-        std::snprintf(msg, sizeof(msg),
-                      "lattice too large for the fixed scratch: %lld tiles x %d particles x 6 "
-                      "doubles exceeds %llu",
-                      ntiles, std::max(n, 1), (unsigned long long)NOALLOC_PARTIAL_DOUBLES);
-        set_err(err, err_len, msg);
-        return LBM_ERR_ARG;
-    }
-
     double maxd = 0.0;
     DevParticle recs[MAX_PARTICLES];
     for (int i = 0; i < n; ++i) {
@@ -146,6 +141,27 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
         d.fixed = p.fixed ? 1.0 : 0.0;
         recs[i] = d;
         maxd = std::max(maxd, p.diameter);
+    }
+    near_grid(g, maxd, L.box);
+    const long long need = near_partial_doubles(L.box, n);
+    if ((unsigned long long)need > (unsigned long long)NOALLOC_PARTIAL_DOUBLES) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg),
+                      "request exceeds the fixed scratch: %lld force-partial doubles needed, "
+                      "%llu available",
+                      need, (unsigned long long)NOALLOC_PARTIAL_DOUBLES);
+        set_err(err, err_len, msg);
+        return LBM_ERR_ARG;
+    }
+    const long long mneed = map_entries(g, maxd, n);
+    if ((unsigned long long)mneed > (unsigned long long)NOALLOC_MAP_ENTRIES) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg),
+                      "request exceeds the fixed scratch: %lld geometry-map entries needed, "
+                      "%llu available",
+                      mneed, (unsigned long long)NOALLOC_MAP_ENTRIES);
+        set_err(err, err_len, msg);
+        return LBM_ERR_ARG;
     }
 
     int dev = 0;
@@ -205,12 +221,10 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     L.parts_prev = a.particles;
     L.partials = a.partials;
     L.status = status_dev ? status_dev : a.status;
+    L.map = a.map;
+    region_extent(g, maxd, L.map_ext);
     L.block = dim3(g.tx, g.ty, 1);
     L.stream = s;
-    const double span = maxd + 2.0 * NEAR_HALO + 1.0;
-    const int T[3] = {g.tx, g.ty, 1};
-    const int nt[3] = {g.ntx, g.nty, g.ntz};
-    for (int k = 0; k < 3; ++k) L.box[k] = std::min((int)std::ceil(span / T[k]) + 2, nt[k]);
 
     if (!status_dev && (e = cudaMemsetAsync(a.status, 0, sizeof(int), s)) != cudaSuccess) {
         set_err(err, err_len, cudaGetErrorString(e));
@@ -220,6 +234,7 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
         e = cudaMemcpyAsync(a.particles, recs, sizeof(DevParticle) * n, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // recs lives on this stack frame
         if (e == cudaSuccess) e = launch_regions(L);
+        if (e == cudaSuccess) e = launch_map(L);
     }
     if (e == cudaSuccess) e = launch_bulk(0, src_pdf_dev, dst_pdf_dev, L);
     if (e == cudaSuccess && n > 0) e = launch_near(0, src_pdf_dev, dst_pdf_dev, L);

@@ -4,8 +4,10 @@ Both sides get the same seeded inputs (paper_1702_04910_gb300.workloads) and
 run the same number of global steps; then the stored post-collision PDFs,
 the hydrodynamic forces and torques, the particle states and the macroscopic
 fields are compared.  Bars (FP64 path): PDFs <= 1e-12 relative to max|f|,
-forces <= 1e-10 relative to |F|.  The FP32 path is compared with a bar
-derived from single-precision rounding (see test_fp32_storage_tracks_fp64).
+forces <= 1e-10 relative to |F|.  The float-float and fixed-point modes
+(FP64 PDFs, collision of cells away from particles in two-float or 64-bit
+fixed-point arithmetic) are held to the same bars.  The FP32 path is compared with a bar derived from single-precision
+rounding (see test_fp32_storage_tracks_fp64).
 """
 import numpy as np
 import pytest
@@ -79,13 +81,14 @@ def compare_particles(o, g, tol=1e-12):
 
 
 # ---- plain fluid (no particles): several tiles with ragged tails -----------------------
+@pytest.mark.parametrize("storage", ["f64", "f64ff", "f64fx"])
 @pytest.mark.parametrize("shape,bc_z,collision", [((37, 21, 9), 0, "TRT"), ((37, 21, 9), 1, "BGK"),
                                                   ((3, 4, 5), 1, "TRT"), ((130, 17, 6), 0, "TRT")])
-def test_fluid_sweep_parity(lattice, shape, bc_z, collision):
+def test_fluid_sweep_parity(lattice, shape, bc_z, collision, storage):
     case = {"shape": shape, "coupling": "NONE", "collision": collision, "tau": 0.73,
             "magic": 3.0 / 16.0, "fext": (1e-5, -2e-6, 3e-6), "gravity": (0, 0, 0), "rho0": 1.0,
             "bc_z": bc_z, "subsample": 4, "subcycles": 1, "wall_contact": 0, "particles": []}
-    o, g = make_pair(case)
+    o, g = make_pair(case, storage=storage)
     start(o, g, lattice, amp=0.05, seed=1)
     o.step(40)
     g.step(40)
@@ -118,10 +121,13 @@ MOVING = [("PSM_M1B1", True), ("PSM_M2B2", True), ("PSM_M3B2", False), ("MEM_BB"
           ("MEM_CLI", True), ("MEM_CLI", False)]
 
 
-@pytest.mark.parametrize("coupling,free", MOVING)
-def test_moving_sphere_parity(lattice, coupling, free):
+@pytest.mark.parametrize("coupling,free,storage",
+                         [m + ("f64",) for m in MOVING] +
+                         [("PSM_M2B2", True, "f64ff"), ("MEM_CLI", True, "f64ff"),
+                          ("PSM_M2B2", True, "f64fx"), ("MEM_CLI", True, "f64fx")])
+def test_moving_sphere_parity(lattice, coupling, free, storage):
     case = moving_sphere_case(coupling, free=free)
-    o, g = make_pair(case)
+    o, g = make_pair(case, storage=storage)
     start(o, g, lattice, amp=0.02, seed=7)
     nsteps = 25
     moved_cells = 0
@@ -180,11 +186,13 @@ def test_periodic_wrap_of_a_sphere(lattice, coupling, free):
 
 
 # ---- the 32^3 fixed-sphere PSM case over its stated 1000 steps -----------------------------------
-@pytest.mark.parametrize("coupling", ["PSM_M1B1", "PSM_M2B2", "PSM_M3B2"])
-def test_fixed_sphere_box_1000_steps(lattice, coupling):
+@pytest.mark.parametrize("coupling,storage", [("PSM_M1B1", "f64"), ("PSM_M2B2", "f64"),
+                                              ("PSM_M3B2", "f64"), ("PSM_M1B1", "f64ff"),
+                                              ("PSM_M1B1", "f64fx")])
+def test_fixed_sphere_box_1000_steps(lattice, coupling, storage):
     case = W.fixed_sphere_box(L=32, D=8.0, tau=0.8, force=4.4e-6, coupling=coupling,
                               collision="TRT")
-    o, g = make_pair(case)
+    o, g = make_pair(case, storage=storage)
     start(o, g, lattice)
     o.step(1000)
     g.step(1000)
@@ -193,10 +201,13 @@ def test_fixed_sphere_box_1000_steps(lattice, coupling):
 
 
 # ---- the 128 x 128 x 512 settling workload at full size, as the benchmark runs it --------
-@pytest.mark.parametrize("coupling", ["MEM_CLI", "PSM_M2B2", "PSM_M3B2"])
-def test_settling_full_size_parity(lattice, coupling):
+@pytest.mark.parametrize("coupling,storage", [("MEM_CLI", "f64"), ("PSM_M2B2", "f64"),
+                                              ("PSM_M3B2", "f64"), ("MEM_CLI", "f64ff"),
+                                              ("PSM_M2B2", "f64ff"), ("MEM_CLI", "f64fx"),
+                                              ("PSM_M2B2", "f64fx")])
+def test_settling_full_size_parity(lattice, coupling, storage):
     case = W.settling_sphere(coupling=coupling)
-    o, g = make_pair(case)
+    o, g = make_pair(case, storage=storage)
     start(o, g, lattice)
     for _ in range(3):
         o.step(1)

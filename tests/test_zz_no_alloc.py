@@ -80,15 +80,19 @@ def test_noalloc_sweep_matches_handle_step(lattice, coupling):
         assert ferr <= FORCE_TOL and terr <= FORCE_TOL, (call, ferr, terr)
 
 
-def test_noalloc_rejects_lattices_beyond_its_scratch():
+def test_noalloc_rejects_requests_beyond_its_scratch():
+    """32 spheres of D = 24 need 32^2 x 120 x 6 doubles of force partials,
+    more than the fixed 524,288: rejected before any device work, so the
+    (deliberately tiny) buffers below are never touched."""
     import torch
 
     from paper_1702_04910_gb300 import binding as B
 
-    cfg = B.make_config((256, 256, 800), coupling="PSM_M1B1", tau=0.8)
+    cfg = B.make_config((256, 256, 256), coupling="PSM_M1B1", tau=0.8)
     dummy = torch.zeros(2, dtype=torch.float64, device="cuda")
-    ft = torch.zeros(6, dtype=torch.float64, device="cuda")
-    parts = [{"x": (128.0, 128.0, 400.0), "diameter": 20.0, "fixed": 1}]
+    ft = torch.zeros(6 * 32, dtype=torch.float64, device="cuda")
+    parts = [{"x": (16.0 + 32.0 * (i % 8), 64.0 + 128.0 * (i // 16), 64.0 + 128.0 * ((i // 8) % 2)),
+              "diameter": 24.0, "fixed": 1} for i in range(32)]
     with pytest.raises(B.LbmError) as ei:
         B.lbm_sweep_noalloc(cfg, dummy.data_ptr(), dummy[1:].data_ptr(), parts, ft.data_ptr())
     assert ei.value.status == B.LBM_ERR_ARG
