@@ -115,21 +115,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def near_tile_cells(particle, shape, tx, ty, halo=2.0):
-    """Cells of the tiles the near-particle kernel takes (host restatement of
-    the library's tiling: tx x ty x 1 tiles, sphere region R + halo)."""
-    import numpy as np
+def max_over_ranks(value: float, dist, device) -> float:
+    """Largest value over all ranks (the whole-job time); identity without a group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, cells: int, sweeps_per_step: int, steps: int, seconds: float) -> float:
+    """Whole-job MLUPS: every rank advances its own replica (weak scaling)."""
+    return world * cells * sweeps_per_step * steps / seconds / 1e6
+
+
+def workload(coupling: str, scale: float):
+    from paper_1702_04910_gb300 import workloads as W
+    if scale == 1.0:
+        return W.settling_sphere(coupling=coupling)
+    return W.scaled_settling_sphere(scale, coupling=coupling)
+
+
+def near_cells(particle, shape, halo=2.0):
+    """Cells the near-particle kernel takes: those whose centre lies within
+    R + halo of the sphere centre along every axis (host restatement of the
+    library's region rule; z is closed)."""
     nx, ny, nz = shape
     R = 0.5 * particle["diameter"]
     count = 1
-    for a, (n, T, periodic) in enumerate(((nx, tx, True), (ny, ty, True), (nz, 1, False))):
+    for a, (n, periodic) in enumerate(((nx, True), (ny, True), (nz, False))):
         X = particle["x"][a]
         lo = math.ceil(X - R - halo - 0.5)
         hi = math.floor(X + R + halo - 0.5)
-        cells = np.arange(lo, hi + 1)
-        cells = np.mod(cells, n) if periodic else cells[(cells >= 0) & (cells < n)]
-        tiles = np.unique(cells // T)
-        count *= sum(min(T, n - t * T) for t in tiles)
+        if not periodic:
+            lo, hi = max(lo, 0), min(hi, n - 1)
+        count *= max(0, min(hi - lo + 1, n))
     return int(count)
 
 
@@ -150,12 +171,13 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream().cuda_stream
-    ncell = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    shape = workload(args.couplings[0], args.scale)["shape"]
+    ncell = shape[0] * shape[1] * shape[2]
 
     def build(storage):
         sims = []
         for cp in args.couplings:
-            case = W.settling_sphere(coupling=cp)
+            case = workload(cp, args.scale)
             s = Simulation(case["shape"], stream=stream, storage=storage, **W.sim_kwargs(case))
             s.set_particles(case["particles"])
             s.init_equilibrium()
@@ -178,11 +200,7 @@ def run_ours(args):
                 s.step(1)
         ev1.record()
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
         profs = [lbm_profile_read(s.h) if profile else None for s in sims]
         return ms, profs
 
@@ -194,7 +212,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         ms, profs = timed(sims, args.steps, True)
     clocks = clk.summary()
-    value = world * ncell * sweeps_per_step * args.steps / (ms * 1e-3) / 1e6
+    value = job_mlups(world, ncell, sweeps_per_step, args.steps, ms * 1e-3)
 
     # dominant kernel: the bulk sweep (events recorded on the library's stream)
     bulk_ms = sum(p["bulk"][0] for p in profs)
@@ -202,10 +220,8 @@ def run_ours(args):
     launches = sum(sum(v[1] for v in p.values()) for p in profs)
     share = {k: sum(p[k][0] for p in profs) for k in PROFILE_CLASSES}
     tot = sum(share.values())
-    tx = 128 if SHAPE[0] >= 128 else (64 if SHAPE[0] >= 64 else 32)
-    ty = 256 // tx
     parts_now = [s.get_particles()[0] for s in sims]
-    near = [near_tile_cells(p, SHAPE, tx, ty) for p in parts_now]
+    near = [near_cells(p, shape) for p in parts_now]
     bulk_cells = sum((ncell - nc) * sweeps_of(c) for nc, c in zip(near, args.couplings)) / sweeps_per_step
     bytes_per_cell = 2 * 19 * 8
     achieved = bytes_per_cell * bulk_cells / (bulk_ms / bulk_n * 1e-3) / 1e9
@@ -226,12 +242,8 @@ def run_ours(args):
             h2d += 11 * 8 + 8
             d2h += 2 * (11 * 8 + 8) + F.nbytes + T.nbytes
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * ncell * sweeps_per_step * args.steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_mlups(world, ncell, sweeps_per_step, args.steps, e2e_s)
 
     # FP64 storage with the collision of cells away from particles in
     # float-float or 64-bit fixed-point arithmetic: speed and error against FP64
@@ -273,42 +285,45 @@ def run_ours(args):
         for s in s64 + sm:
             s.close()
 
-    # FP32 storage variant and its force / velocity error against FP64
-    if not args.no_fp32:
-        sims64 = build("f64")
-        sims32 = build("f32")
+    # FP32 / shifted FP16 / shifted BF16 storage (FP32 collision): speed and
+    # force / particle-velocity error against the FP64 run
+    lowp = {"f32": (4, "FP32 PDFs, FP32 collision"),
+            "f16s": (2, "FP16 shifted populations f - w_q, FP32 collision"),
+            "bf16s": (2, "BF16 shifted populations f - w_q, FP32 collision")}
+    for mode in ([] if args.no_fp32 else ["f32", "f16s", "bf16s"]):
+        esize, what = lowp[mode]
+        simsl = build(mode)
         for _ in range(args.warmup):
-            for s in sims32:
+            for s in simsl:
                 s.step(1)
-        ms32, profs32 = timed(sims32, args.steps, True)
-        v32 = world * ncell * sweeps_per_step * args.steps / (ms32 * 1e-3) / 1e6
-        b32 = sum(p["bulk"][0] for p in profs32) / sum(p["bulk"][1] for p in profs32)
-        ach32 = 2 * 19 * 4 * bulk_cells / (b32 * 1e-3) / 1e9
-        # accuracy: fresh pair, same start, args.acc_steps steps
-        for s in sims32:
+        msl, profsl = timed(simsl, args.steps, True)
+        vl = job_mlups(world, ncell, sweeps_per_step, args.steps, msl * 1e-3)
+        bl = sum(p["bulk"][0] for p in profsl) / sum(p["bulk"][1] for p in profsl)
+        achl = 2 * 19 * esize * bulk_cells / (bl * 1e-3) / 1e9
+        for s in simsl:
             s.close()
-        sims32 = build("f32")
-        nacc = args.acc_steps
-        for s64, s32 in zip(sims64, sims32):
-            s64.step(nacc)
-            s32.step(nacc)
+        s64, sl = build("f64"), build(mode)
+        for a, b in zip(s64, sl):
+            a.step(args.acc_steps)
+            b.step(args.acc_steps)
         ferr, verr = {}, {}
-        for c, s64, s32 in zip(args.couplings, sims64, sims32):
-            F64, _ = s64.forces()
-            F32, _ = s32.forces()
-            p64, p32 = s64.get_particles()[0], s32.get_particles()[0]
-            ferr[c] = float(np.linalg.norm(F32 - F64) / max(np.linalg.norm(F64), 1e-300))
-            verr[c] = float(np.linalg.norm(p32["u"] - p64["u"]) / max(np.linalg.norm(p64["u"]), 1e-300))
-        variants["f32"] = {"value": v32, "unit": "MLUPS", "ms_per_step": ms32 / args.steps,
-                           "bulk_GBps": ach32, "frac": ach32 / peak,
-                           "force_rel_err_vs_f64": ferr, "particle_velocity_rel_err_vs_f64": verr,
-                           "after_steps": nacc}
-        for s in sims64 + sims32:
+        for c, a, b in zip(args.couplings, s64, sl):
+            Fa, _ = a.forces()
+            Fb, _ = b.forces()
+            pa, pb = a.get_particles()[0], b.get_particles()[0]
+            ferr[c] = float(np.linalg.norm(Fb - Fa) / max(np.linalg.norm(Fa), 1e-300))
+            verr[c] = float(np.linalg.norm(pb["u"] - pa["u"]) / max(np.linalg.norm(pa["u"]), 1e-300))
+        variants[mode] = {"value": vl, "unit": "MLUPS", "ms_per_step": msl / args.steps,
+                          "bulk_GBps": achl, "frac": achl / peak, "bulk_avg_launch_ms": bl,
+                          "algorithmic_bytes_per_cell": 2 * 19 * esize, "arithmetic": what,
+                          "force_rel_err_vs_f64": ferr, "particle_velocity_rel_err_vs_f64": verr,
+                          "after_steps": args.acc_steps}
+        for s in s64 + sl:
             s.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_sample_steps)
+        cpu = cpu_baseline(args.cpu_sample_steps, args.scale)
 
     if rank == 0:
         line = {
@@ -316,7 +331,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded workload, no dataset)",
-            "config": {"workload": WORKLOAD, "shape": list(SHAPE), "couplings": list(args.couplings),
+            "config": {"workload": WORKLOAD if args.scale == 1.0 else f"{WORKLOAD} (scaled by {args.scale})",
+                       "shape": list(shape), "couplings": list(args.couplings),
                        "lbm_sweeps_per_step": sweeps_per_step, "collision": "TRT (Lambda=3/16)",
                        "precision": "FP64 PDFs and collision; FP64 forces and rigid-body update",
                        "l2": "inputs larger than L2 (2.55 GB of PDFs per simulation)",
@@ -352,12 +368,12 @@ def oracle_sample_step(sims):
         o.step(1)
 
 
-def build_oracles():
+def build_oracles(scale: float = 1.0):
     from oracle.oracle import Oracle
     from paper_1702_04910_gb300 import workloads as W
     sims = []
     for cp in COUPLINGS:
-        case = W.settling_sphere(coupling=cp)
+        case = workload(cp, scale)
         o = Oracle(case["shape"], **W.sim_kwargs(case))
         o.set_particles(case["particles"])
         o.init_equilibrium()
@@ -365,16 +381,17 @@ def build_oracles():
     return sims
 
 
-def cpu_baseline(steps: int):
+def cpu_baseline(steps: int, scale: float = 1.0):
     """The FP64 oracle (as it stands) on the same workload: `steps` global steps
-    of the five variants on the full 128x128x512 domain, host cores."""
-    sims = build_oracles()
+    of the four variants on the full domain, host cores."""
+    sims = build_oracles(scale)
     t0 = time.perf_counter()
     for _ in range(steps):
         oracle_sample_step(sims)
     dt = time.perf_counter() - t0
     sweeps = sum(sweeps_of(c) for c in COUPLINGS)
-    ncell = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    shape = sims[0].shape
+    ncell = shape[0] * shape[1] * shape[2]
     for o in sims:
         o.close()
     return {"value": ncell * sweeps * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle_threads(),
@@ -388,7 +405,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sims = build_oracles()
+    sims = build_oracles(args.scale)
     for _ in range(args.warmup):
         oracle_sample_step(sims)
     t0 = time.perf_counter()
@@ -396,7 +413,8 @@ def run_reference(args):
         oracle_sample_step(sims)
     dt = time.perf_counter() - t0
     sweeps = sum(sweeps_of(c) for c in COUPLINGS)
-    ncell = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    shape = sims[0].shape
+    ncell = shape[0] * shape[1] * shape[2]
     value = ncell * sweeps * args.steps / dt / 1e6
     world = int(os.environ.get("WORLD_SIZE", "1"))
     sample = (f"each step: one global step of the four variants on the full 128x128x512 domain "
@@ -405,7 +423,8 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded workload, no dataset)",
-            "config": {"workload": WORKLOAD, "shape": list(SHAPE), "couplings": list(COUPLINGS),
+            "config": {"workload": WORKLOAD if args.scale == 1.0 else f"{WORKLOAD} (scaled by {args.scale})",
+                       "shape": list(shape), "couplings": list(COUPLINGS),
                        "lbm_sweeps_per_step": sweeps},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle_threads(),
                              "kind": "oracle", "sample": sample},
@@ -453,9 +472,12 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the settling workload by this factor in every length (tests)")
     ap.add_argument("--case-shape", default=None,
                     help="run a single small profiling case of this shape (e.g. 128x128x256)")
-    ap.add_argument("--case-storage", default="f64", choices=("f64", "f32", "f64ff", "f64fx"))
+    ap.add_argument("--case-storage", default="f64",
+                    choices=("f64", "f32", "f64ff", "f64fx", "f16s", "bf16s"))
     args = ap.parse_args()
     args.couplings = tuple(c for c in args.couplings.split(",") if c)
     if args.warmup < 3:

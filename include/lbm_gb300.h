@@ -82,12 +82,17 @@ typedef enum { LBM_BGK = 0, LBM_TRT = 1 } lbm_collision;
  *                     runs in 64-bit fixed point (value = integer * 2^-58:
  *                     exact sums, products to 2^-58), converted from and to
  *                     FP64 with integer operations; cells near particles use
- *                     FP64.  Same state layout as LBM_STORE_F64. */
+ *                     FP64.  Same state layout as LBM_STORE_F64.
+ *   LBM_STORE_F16S    PDFs stored as FP16 shifted populations f_q - w_q, FP32
+ *                     collision arithmetic (76 B per cell update).
+ *   LBM_STORE_BF16S   the same with BF16 storage. */
 typedef enum {
     LBM_STORE_F64 = 0,
     LBM_STORE_F32 = 1,
     LBM_STORE_F64_FF = 2,
-    LBM_STORE_F64_FX = 3
+    LBM_STORE_F64_FX = 3,
+    LBM_STORE_F16S = 4,
+    LBM_STORE_BF16S = 5
 } lbm_storage;
 
 typedef struct {
@@ -120,12 +125,14 @@ typedef struct lbm_handle lbm_handle;
 
 /* Field selectors of lbm_get_fields / lbm_set_fields. */
 enum {
-    LBM_FIELD_PDF = 0,     /* stored post-collision PDFs (state), 19*N of the storage type */
+    LBM_FIELD_PDF = 0,     /* stored post-collision PDFs (state), 19*N of the storage type
+                              (FP16/BF16 modes: the shifted values f_q - w_q) */
     LBM_FIELD_PDF_PRE = 1, /* set only: pre-collision PDFs f at t = 0, 19*N doubles        */
     LBM_FIELD_RHO = 2,     /* get only: fluid density rho_f, N doubles                     */
     LBM_FIELD_U = 3,       /* get only: velocity u, Eq. (8) / (27), 3*N doubles [cell][3]   */
     LBM_FIELD_EPS = 4,     /* get only: PSM solid fraction sum_s eps_s, N doubles          */
-    LBM_FIELD_FLAG = 5     /* get only: MEM owner (0 fluid, s+1 inside particle s), N int32 */
+    LBM_FIELD_FLAG = 5,    /* get only: MEM owner (0 fluid, s+1 inside particle s), N int32 */
+    LBM_FIELD_PDF_F64 = 6  /* get only: the stored PDFs as FP64 values of f (shift undone) */
 };
 
 /* Create a simulation.  Validates *cfg (LBM_ERR_ARG on a bad value,
@@ -245,6 +252,94 @@ lbm_status lbm_sweep_noalloc(const lbm_config *cfg, const double *src_pdf_dev,
                              double *dst_pdf_dev, int n, const lbm_particle *particles_host,
                              double *force_torque_dev, int *status_dev, void *stream,
                              char *err, size_t err_len);
+
+/* ---- batched ensemble -------------------------------------------------------
+ * Many independent single-sphere cases (each its own lattice, configuration
+ * and particle) advanced together on one GPU.  This is how ensembles of
+ * settling cases (uneven domain sizes and Galileo numbers, Sec. 4 of the
+ * paper studies one case at a time) are produced at full-GPU occupancy:
+ *   - every kernel of a global step is one launch over all cases (work items
+ *     of the cases concatenated; each block finds its case by binary search
+ *     over the prefix sums of the per-case item counts);
+ *   - the bulk sweep is a persistent kernel whose blocks stride over the
+ *     tiles of all cases; the near-particle sweep runs beside it;
+ *   - the launches of one global step are captured once into a CUDA graph
+ *     and replayed by lbm_batch_step;
+ *   - lbm_batch_autotune times the bulk sweep for each tile layout and grid
+ *     size and keeps the fastest (results do not depend on the choice).
+ * Each case follows the step contract of lbm_step (MEM: lbm_subcycles
+ * sweeps, averaged forces, rigid-body update with dt = subcycles, refilling;
+ * PSM: one sweep, dt = 1).  The stored state of every case starts as the
+ * fluid at rest, f~ = f_eq(rho0, 0) (Eq. (3)), taken as the post-collision
+ * field of step 0. */
+typedef struct lbm_batch lbm_batch;
+
+/* Bulk-sweep tile layouts of lbm_batch_set_tuning. */
+enum {
+    LBM_BATCH_BOX32 = 0,  /* 32 x 8 cell tiles of one z plane                  */
+    LBM_BATCH_BOX64 = 1,  /* 64 x 4                                            */
+    LBM_BATCH_BOX128 = 2, /* 128 x 2                                           */
+    LBM_BATCH_PLANE = 3   /* 256 consecutive cells of an xy plane (x fastest)  */
+};
+
+/* Creates a batch of n_cases (1..4096) cases.
+ *   cfgs[c]       configuration of case c (as for lbm_create); coupling must
+ *                 be a PSM variant, LBM_MEM_BB or LBM_MEM_CLI; storage must
+ *                 be LBM_STORE_F64 or LBM_STORE_F64_FX and the same for every
+ *                 case.
+ *   particles[c]  the one sphere of case c (copied).
+ *   stream        cudaStream_t or NULL: stream of every batch call.
+ * All device memory of the batch is one allocation (PDF buffers, particle
+ * records, force partials and geometry maps, 256-byte aligned slices).
+ * Returns LBM_ERR_ARG for an invalid case (nothing is allocated),
+ * LBM_ERR_OOM when the allocation fails. */
+lbm_status lbm_batch_create(int n_cases, const lbm_config *cfgs, const lbm_particle *particles,
+                            void *stream, lbm_batch **out);
+
+/* Enqueues nsteps global steps of every case (graph replays; asynchronous). */
+lbm_status lbm_batch_step(lbm_batch *b, int nsteps);
+
+/* Times the bulk sweep of every layout (LBM_BATCH_*) and grid size (one block
+ * per tile, or 1x, 2x, 4x the resident blocks of the GPU) with `reps`
+ * launches each (1..100), keeps the fastest and rebuilds the step graph.  The
+ * timed launches write only the buffer the next sweep overwrites, so the
+ * simulation state is unchanged.  Outputs (each may be NULL): the chosen
+ * layout, grid (0 = one block per tile) and its mean launch time in ms. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *layout, int *grid, double *ms);
+
+/* Sets the bulk layout (LBM_BATCH_*) and grid (0 = one block per tile, else
+ * the number of persistent blocks) explicitly and rebuilds the step graph. */
+lbm_status lbm_batch_set_tuning(lbm_batch *b, int layout, int grid);
+
+/* Particle state of every case (n_cases records; synchronises). */
+lbm_status lbm_batch_get_particles(lbm_batch *b, lbm_particle *host_out);
+
+/* Hydrodynamic force and torque of the last step of every case, as for
+ * lbm_get_forces: F and T each n_cases x 3 doubles (synchronises). */
+lbm_status lbm_batch_get_forces(lbm_batch *b, double *F, double *T);
+
+/* Stored post-collision PDFs of case c (19 * N_c doubles, layout of
+ * LBM_FIELD_PDF) into host memory; bytes must equal 19 * N_c * 8. */
+lbm_status lbm_batch_get_pdf(lbm_batch *b, int c, double *host_out, size_t bytes);
+
+/* Lattice cell updates per global step, summed over the cases (MEM cases
+ * count each sweep). */
+long long lbm_batch_cell_updates(const lbm_batch *b);
+
+/* Device bytes held by the batch. */
+size_t lbm_batch_device_bytes(const lbm_batch *b);
+
+/* Number of kernel launches in one global step's graph. */
+int lbm_batch_graph_kernels(const lbm_batch *b);
+
+/* Waits for the batch's stream; reports a raised device status. */
+lbm_status lbm_batch_synchronize(lbm_batch *b);
+
+void lbm_batch_destroy(lbm_batch *b);
+
+/* Message of the last failure on b; with b == NULL, why the calling thread's
+ * last lbm_batch_create failed (empty after a success). */
+const char *lbm_batch_last_error(const lbm_batch *b);
 
 #ifdef __cplusplus
 }

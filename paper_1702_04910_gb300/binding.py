@@ -29,8 +29,8 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR
 COUPLING = {"PSM_M1B1": 0, "PSM_M2B2": 1, "PSM_M3B2": 2, "MEM_BB": 3, "MEM_CLI": 4,
             "MEM_MR": 5, "NONE": 6}
 COLLISION = {"BGK": 0, "TRT": 1}
-STORAGE = {"f64": 0, "f32": 1, "f64ff": 2, "f64fx": 3}
-FIELD_PDF, FIELD_PDF_PRE, FIELD_RHO, FIELD_U, FIELD_EPS, FIELD_FLAG = range(6)
+STORAGE = {"f64": 0, "f32": 1, "f64ff": 2, "f64fx": 3, "f16s": 4, "bf16s": 5}
+FIELD_PDF, FIELD_PDF_PRE, FIELD_RHO, FIELD_U, FIELD_EPS, FIELD_FLAG, FIELD_PDF_F64 = range(7)
 PROFILE_CLASSES = ("bulk", "near", "force_total", "rigid_body", "refill", "other")
 
 EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_equilibrium",
@@ -257,7 +257,16 @@ class Simulation:
 
     @property
     def pdf_dtype(self):
-        return np.float32 if self.storage == "f32" else np.float64
+        """NumPy dtype of the stored PDF array (16-bit formats: raw bits)."""
+        return {"f32": np.float32, "f16s": np.float16, "bf16s": np.uint16}.get(self.storage,
+                                                                               np.float64)
+
+    def pdf_f64(self) -> np.ndarray:
+        """Stored post-collision PDFs as FP64 values of f (converted on the GPU)."""
+        nx, ny, nz = self.shape
+        out = np.empty((NQ, nz, ny, nx), dtype=np.float64)
+        lbm_get_fields(self.h, FIELD_PDF_F64, out.ctypes.data, out.nbytes, False)
+        return out
 
     def set_particles(self, particles):
         lbm_set_particles(self.h, particles)

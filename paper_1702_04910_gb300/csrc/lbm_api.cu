@@ -40,6 +40,8 @@ struct EventPair {
 struct lbm_handle {
     lbm_config cfg;
     cudaStream_t stream;
+    cudaStream_t side;           // private stream: near-particle sweep runs beside k_bulk
+    cudaEvent_t ev_fork, ev_join;
     int device;
     Geom g;
     int storage;       // 0 FP64, 1 FP32 (PDF storage / arithmetic of every kernel but k_bulk)
@@ -110,16 +112,17 @@ cudaEvent_t take_event(lbm_handle* h) {
 }
 
 // Records an event before a launch when profiling; returns the pair index.
-int prof_begin(lbm_handle* h, int cls) {
+// The pair is recorded on the stream the kernel is launched on.
+int prof_begin(lbm_handle* h, int cls, cudaStream_t s = nullptr) {
     if (!h->profiling) return -1;
     EventPair p{take_event(h), take_event(h), cls};
     if (!p.a || !p.b) return -1;
-    cudaEventRecord(p.a, h->stream);
+    cudaEventRecord(p.a, s ? s : h->stream);
     h->events.push_back(p);
     return (int)h->events.size() - 1;
 }
-void prof_end(lbm_handle* h, int i) {
-    if (i >= 0) cudaEventRecord(h->events[i].b, h->stream);
+void prof_end(lbm_handle* h, int i, cudaStream_t s = nullptr) {
+    if (i >= 0) cudaEventRecord(h->events[i].b, s ? s : h->stream);
 }
 
 Launch base_launch(lbm_handle* h) {
@@ -147,37 +150,6 @@ Launch base_launch(lbm_handle* h) {
     L.map = h->d_map;
     region_extent(h->g, h->maxd, L.map_ext);
     return L;
-}
-
-// Collision constants (computed in FP64, rounded once to C).
-template <typename C>
-Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) {
-    Coll<C> k{};
-    k.lam_p = (C)lp;
-    k.lam_m = (C)lm;
-    k.rho0 = (C)rho0;
-    k.inv_rho0 = (C)(1.0 / rho0);
-    k.fx = (C)fe[0];
-    k.fy = (C)fe[1];
-    k.fz = (C)fe[2];
-    k.has_force = (fe[0] != 0.0 || fe[1] != 0.0 || fe[2] != 0.0);
-    k.alpha = (C)(1.0 + 0.5 * (lp + lm));
-    k.beta = (C)(0.5 * (lp - lm));
-    k.c0 = (C)(1.0 + lp);
-    k.m15r0 = (C)(-1.5 * rho0);
-    const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
-    for (int c = 0; c < 3; ++c) {
-        k.lpw[c] = (C)(lp * w[c]);
-        k.k1w[c] = (C)(4.5 * lp * w[c] * rho0);
-        k.k2w[c] = (C)(3.0 * lm * w[c] * rho0);
-        k.hw[c] = (C)(3.0 * w[c]);
-    }
-    for (int q = 1; q < NQ; q += 2) {
-        const double cf = cx(q) * fe[0] + cy(q) * fe[1] + cz(q) * fe[2];
-        k.gq[(q - 1) / 2] = (C)(9.0 * wq(q) * cf);
-        k.fq[(q - 1) / 2] = (C)(3.0 * wq(q) * cf);
-    }
-    return k;
 }
 
 lbm_status free_particles(lbm_handle* h) {
@@ -263,14 +235,22 @@ lbm_status sweep(lbm_handle* h, int sub) {
     L.partials = h->d_partials + (size_t)sub * (size_t)near_partial_doubles(L.box, h->np);
     const void* src = h->buf[h->cur];
     void* dst = h->buf[1 - h->cur];
+    // The near-particle cells and the bulk cells are disjoint: the (small,
+    // latency-bound) near sweep runs on a private stream beside k_bulk.
+    if (h->np > 0) {
+        CK(h, cudaEventRecord(h->ev_fork, h->stream), "fork record");
+        CK(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
+        Launch Ln = L;
+        Ln.stream = h->side;
+        int pn = prof_begin(h, PC_NEAR, h->side);
+        CK(h, launch_near(h->storage, src, dst, Ln), "near sweep launch");
+        prof_end(h, pn, h->side);
+        CK(h, cudaEventRecord(h->ev_join, h->side), "join record");
+    }
     int pi = prof_begin(h, PC_BULK);
     CK(h, launch_bulk(h->bulk_mode, src, dst, L), "bulk sweep launch");
     prof_end(h, pi);
-    if (h->np > 0) {
-        pi = prof_begin(h, PC_NEAR);
-        CK(h, launch_near(h->storage, src, dst, L), "near sweep launch");
-        prof_end(h, pi);
-    }
+    if (h->np > 0) CK(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
     h->cur = 1 - h->cur;
     h->pending_pre = 0;
     return LBM_OK;
@@ -352,9 +332,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     if (!(cfg->tau > 0.5) || !(cfg->rho0 > 0.0) || !std::isfinite(cfg->tau)) return LBM_ERR_ARG;
     if (cfg->coupling < 0 || cfg->coupling > LBM_NONE) return LBM_ERR_ARG;
     if (cfg->collision != LBM_BGK && cfg->collision != LBM_TRT) return LBM_ERR_ARG;
-    if (cfg->storage != LBM_STORE_F64 && cfg->storage != LBM_STORE_F32 &&
-        cfg->storage != LBM_STORE_F64_FF && cfg->storage != LBM_STORE_F64_FX)
-        return LBM_ERR_ARG;
+    if (cfg->storage < LBM_STORE_F64 || cfg->storage > LBM_STORE_BF16S) return LBM_ERR_ARG;
     if (cfg->bc_z != 0 && cfg->bc_z != 1) return LBM_ERR_ARG;
     if (cfg->subsample < 0 || cfg->subsample > 40 || cfg->lbm_subcycles < 0) return LBM_ERR_ARG;
     if (cfg->coupling == LBM_MEM_MR) return LBM_ERR_UNSUPPORTED;
@@ -374,12 +352,23 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     if (h->cfg.subsample == 0) h->cfg.subsample = 4;
     h->stream = (cudaStream_t)stream;
     cudaGetDevice(&h->device);
-    h->storage = cfg->storage == LBM_STORE_F32 ? 1 : 0;
-    h->bulk_mode = cfg->storage == LBM_STORE_F32      ? 1
-                   : cfg->storage == LBM_STORE_F64_FF ? 2
-                   : cfg->storage == LBM_STORE_F64_FX ? 3
-                                                      : 0;
-    h->esize = h->storage == 0 ? sizeof(double) : sizeof(float);
+    {
+        cudaError_t e0 = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e0 != cudaSuccess) {
+            lbm_status st0 = cuda_fail(h, e0, "stream / event creation");
+            lbm_destroy(h);
+            return st0;
+        }
+    }
+    // kernel storage codes: 0 FP64, 1 FP32, 4 FP16 shifted, 5 BF16 shifted
+    h->storage = cfg->storage == LBM_STORE_F32     ? 1
+                 : cfg->storage == LBM_STORE_F16S  ? 4
+                 : cfg->storage == LBM_STORE_BF16S ? 5
+                                                   : 0;
+    h->esize = h->storage == 0 ? sizeof(double) : (h->storage == 1 ? sizeof(float) : 2);
+    h->bulk_mode = cfg->storage;  // bulk arithmetic: the storage code, or 2 / 3 on FP64 state
     h->kind = is_psm(cfg->coupling) ? 1 : (is_mem(cfg->coupling) ? 2 : 0);
     h->variant = h->kind == 1 ? cfg->coupling - LBM_PSM_M1B1
                               : (h->kind == 2 ? cfg->coupling - LBM_MEM_BB : 0);
@@ -396,7 +385,8 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     g.ty = 256 / g.tx;
     g.ntx = (cfg->nx + g.tx - 1) / g.tx;
     g.nty = (cfg->ny + g.ty - 1) / g.ty;
-    g.ntz = cfg->nz;
+    g.tz = cfg->storage == LBM_STORE_F32 ? 2 : 1;  // two z cells per thread (k_bulk)
+    g.ntz = (cfg->nz + g.tz - 1) / g.tz;
 
     const double lp = -1.0 / cfg->tau;
     const double lm = cfg->collision == LBM_TRT ? 1.0 / (cfg->magic / (0.5 + 1.0 / lp) - 0.5) : lp;
@@ -434,6 +424,12 @@ void lbm_destroy(lbm_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
     cudaFree(h->d_status);
@@ -594,6 +590,7 @@ lbm_status lbm_get_fields(lbm_handle* h, int what, void* dst, size_t bytes, int 
         case LBM_FIELD_EPS: need = n * sizeof(double); break;
         case LBM_FIELD_U: need = 3 * n * sizeof(double); break;
         case LBM_FIELD_FLAG: need = n * sizeof(int); break;
+        case LBM_FIELD_PDF_F64: need = (size_t)NQ * n * sizeof(double); break;
         default: return fail(h, LBM_ERR_ARG, "unknown field");
     }
     if (bytes != need) return fail(h, LBM_ERR_ARG, "byte count does not match the field");
@@ -608,7 +605,10 @@ lbm_status lbm_get_fields(lbm_handle* h, int what, void* dst, size_t bytes, int 
     if (!dst_is_device) CK(h, cudaMalloc(&out, need), "cudaMalloc field");
     Launch L = base_launch(h);
     L.nostream = h->pending_pre;
-    cudaError_t e = launch_macro(h->storage, h->buf[h->cur], L, what, out);
+    cudaError_t e = what == LBM_FIELD_PDF_F64
+                        ? launch_to_f64(h->storage, h->buf[h->cur], (double*)out,
+                                        (long long)NQ * (long long)n, (long long)n, h->stream)
+                        : launch_macro(h->storage, h->buf[h->cur], L, what, out);
     if (e == cudaSuccess && !dst_is_device)
         e = cudaMemcpyAsync(dst, out, need, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -645,8 +645,8 @@ lbm_status lbm_set_fields(lbm_handle* h, int what, const void* src, size_t bytes
             }
             dsrc = tmp;
         }
-        cudaError_t e = launch_from_f64(h->storage, dsrc, h->buf[h->cur], (long long)NQ * (long long)n,
-                                        h->stream);
+        cudaError_t e = launch_from_f64(h->storage, dsrc, h->buf[h->cur],
+                                        (long long)NQ * (long long)n, (long long)n, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (tmp) cudaFree(tmp);
         if (e != cudaSuccess) return cuda_fail(h, e, "field conversion");

@@ -12,8 +12,12 @@
 // 32 consecutive x reads and writes 32 consecutive elements per direction.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "lbm_fixed.cuh"
 
 namespace lbmgpu {
 
@@ -57,7 +61,8 @@ struct Geom {
     int nx, ny, nz;
     int bc_z;           // 1: closed resting walls at z = 0 and z = nz
     long long n;        // cells
-    int tx, ty;         // tile extent (= block dims)
+    int tx, ty;         // tile extent in x, y (= block dims)
+    int tz;             // z planes per tile (cells per thread along z in k_bulk)
     int ntx, nty, ntz;  // tiles per axis
 };
 
@@ -224,7 +229,7 @@ __device__ inline NearRegion near_region(const Geom& g, const DevParticle& P) {
     NearRegion nr;
     nr.ax[0] = axis_range(P.x[0], P.r, g.nx, g.tx, g.ntx, true);
     nr.ax[1] = axis_range(P.x[1], P.r, g.ny, g.ty, g.nty, true);
-    nr.ax[2] = axis_range(P.x[2], P.r, g.nz, 1, g.ntz, !g.bc_z);
+    nr.ax[2] = axis_range(P.x[2], P.r, g.nz, g.tz, g.ntz, !g.bc_z);
     return nr;
 }
 
@@ -301,59 +306,140 @@ __device__ __forceinline__ long long lin(const Geom& g, int x, int y, int z) {
     return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
 }
 
+// ---- PDF storage --------------------------------------------------------------
+// FP64 / FP32 store f_q itself.  The 16-bit formats store the shifted
+// population f_q - w_q (rho0 = 1 reference state) so that the stored value is
+// the small deviation from rest; loads add w_q back in FP32.
 template <typename T>
-__device__ __forceinline__ double ld(const T* p) {
-    return (double)__ldg(p);
+struct PdfStore {
+    template <typename C>
+    __device__ __forceinline__ static C load(const T* p, int) {
+        return (C)__ldg(p);
+    }
+    template <typename C>
+    __device__ __forceinline__ static T save(C v, int) {
+        return (T)v;
+    }
+};
+template <>
+struct PdfStore<__half> {
+    template <typename C>
+    __device__ __forceinline__ static C load(const __half* p, int q) {
+        return (C)(__half2float(__ldg(p)) + (float)wq(q));
+    }
+    template <typename C>
+    __device__ __forceinline__ static __half save(C v, int q) {
+        return __float2half_rn((float)v - (float)wq(q));
+    }
+};
+template <>
+struct PdfStore<__nv_bfloat16> {
+    template <typename C>
+    __device__ __forceinline__ static C load(const __nv_bfloat16* p, int q) {
+        return (C)(__bfloat162float(__ldg(p)) + (float)wq(q));
+    }
+    template <typename C>
+    __device__ __forceinline__ static __nv_bfloat16 save(C v, int q) {
+        return __float2bfloat16_rn((float)v - (float)wq(q));
+    }
+};
+
+// Arithmetic type of the kernels that work on a storage type.
+template <typename T> struct ComputeOf { using type = T; };
+template <> struct ComputeOf<__half> { using type = float; };
+template <> struct ComputeOf<__nv_bfloat16> { using type = float; };
+
+template <typename T>
+__device__ __forceinline__ double ld_pdf(const T* p, int q) {
+    return PdfStore<T>::template load<double>(p, q);
+}
+
+// Linear-index offsets from a cell to its neighbours along each axis, with
+// the periodic wrap folded in (z offsets 64-bit); zlo / zhi mark a closed
+// wall just below / above the cell.
+struct NbrOff {
+    int dxm, dxp, dym, dyp;
+    long long dzm, dzp;
+    bool zlo, zhi;
+};
+
+__device__ __forceinline__ NbrOff make_off(const Geom& g, int x, int y, int z) {
+    NbrOff o;
+    o.dxm = x == 0 ? g.nx - 1 : -1;
+    o.dxp = x == g.nx - 1 ? 1 - g.nx : 1;
+    o.dym = y == 0 ? (g.ny - 1) * g.nx : -g.nx;
+    o.dyp = y == g.ny - 1 ? (1 - g.ny) * g.nx : g.nx;
+    const long long sz = (long long)g.nx * g.ny;
+    o.zlo = g.bc_z && z == 0;
+    o.zhi = g.bc_z && z == g.nz - 1;
+    if (g.bc_z) {
+        o.dzm = -sz;
+        o.dzp = sz;
+    } else {
+        o.dzm = z == 0 ? (long long)(g.nz - 1) * sz : -sz;
+        o.dzp = z == g.nz - 1 ? -(long long)(g.nz - 1) * sz : sz;
+    }
+    return o;
+}
+
+// Index offset of the upstream cell x - c_Q.
+template <int Q>
+__device__ __forceinline__ long long upstream_off(const NbrOff& o) {
+    long long d = 0;
+    if (cx(Q) > 0) d += o.dxm;
+    else if (cx(Q) < 0) d += o.dxp;
+    if (cy(Q) > 0) d += o.dym;
+    else if (cy(Q) < 0) d += o.dyp;
+    if (cz(Q) > 0) d += o.dzm;
+    else if (cz(Q) < 0) d += o.dzp;
+    return d;
 }
 
 // Plain pull of all 19 values for a fluid cell that has no particle link:
 // periodic neighbours, halfway bounce-back at resting closed walls.
 template <typename T, typename C, int Q>
-__device__ __forceinline__ void pull_one(const T* __restrict__ src, const Geom& g, const Nbr& b,
-                                         int x, int y, int z, long long idx, C (&f)[NQ]) {
-    int xs, ys, zs;
-    shifted<Q>(b, x, y, z, -1, xs, ys, zs);
-    if (cz(Q) != 0 && (zs < 0 || zs >= g.nz)) {
-        f[Q] = (C)__ldg(src + (long long)opp(Q) * g.n + idx);
+__device__ __forceinline__ void pull_one(const T* __restrict__ src, const Geom& g,
+                                         const NbrOff& o, long long idx, C (&f)[NQ]) {
+    if ((cz(Q) > 0 && o.zlo) || (cz(Q) < 0 && o.zhi)) {
+        f[Q] = PdfStore<T>::template load<C>(src + (long long)opp(Q) * g.n + idx, opp(Q));
     } else {
-        f[Q] = (C)__ldg(src + (long long)Q * g.n + lin(g, xs, ys, zs));
+        f[Q] = PdfStore<T>::template load<C>(src + (long long)Q * g.n + idx + upstream_off<Q>(o), Q);
     }
 }
 
 template <typename T, typename C, int Q>
 struct PullAll {
     __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
-                                               const Nbr& b, int x, int y, int z, long long idx,
-                                               C (&f)[NQ]) {
-        pull_one<T, C, Q>(src, g, b, x, y, z, idx, f);
-        PullAll<T, C, Q + 1>::run(src, g, b, x, y, z, idx, f);
+                                               const NbrOff& o, long long idx, C (&f)[NQ]) {
+        pull_one<T, C, Q>(src, g, o, idx, f);
+        PullAll<T, C, Q + 1>::run(src, g, o, idx, f);
     }
 };
 template <typename T, typename C>
 struct PullAll<T, C, NQ> {
-    __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const Nbr&, int,
-                                               int, int, long long, C (&)[NQ]) {}
+    __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const NbrOff&,
+                                               long long, C (&)[NQ]) {}
 };
 
 template <typename T, typename C>
 __device__ __forceinline__ void pull_plain(const T* __restrict__ src, const Geom& g, int x, int y,
                                            int z, long long idx, C (&f)[NQ]) {
-    Nbr b = make_nbr(g, x, y, z);
-    PullAll<T, C, 0>::run(src, g, b, x, y, z, idx, f);
+    const NbrOff o = make_off(g, x, y, z);
+    PullAll<T, C, 0>::run(src, g, o, idx, f);
 }
 
 template <typename T, typename C>
 __device__ __forceinline__ void load_own(const T* __restrict__ src, const Geom& g, long long idx,
                                          C (&f)[NQ]) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) f[q] = (C)__ldg(src + (long long)q * g.n + idx);
+    for (int q = 0; q < NQ; ++q) f[q] = PdfStore<T>::template load<C>(src + (long long)q * g.n + idx, q);
 }
 
 template <typename T, typename C>
 __device__ __forceinline__ void store_own(T* __restrict__ dst, const Geom& g, long long idx,
                                           const C (&f)[NQ]) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + idx] = (T)f[q];
+    for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + idx] = PdfStore<T>::template save<C>(f[q], q);
 }
 
 // ---- moments Eq. (4) ---------------------------------------------------------

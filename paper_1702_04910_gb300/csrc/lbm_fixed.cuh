@@ -5,8 +5,8 @@
 // relaxation constants, all well inside +-32), so it can run on the integer
 // pipes in fixed point: a value x is the signed 64-bit integer round(x 2^58).
 //   + and -   exact two-instruction integer adds;
-//   *         the 128-bit product shifted right by 58 (floor: error below
-//             2^-58 ~ 3.5e-18, far under FP64 rounding of O(0.1) values);
+//   *         32 x 32 -> 64-bit partial products, rounded to nearest at
+//             2^-58: unbiased, error within 1 unit of 2^-58 (3.5e-18);
 //   FP64 in   the 53-bit significand shifted by the exponent (integer ops);
 //   FP64 out  normalised with a leading-zero count, rounded to nearest.
 // Values of magnitude >= 32 saturate on input (the state is then unphysical
@@ -18,6 +18,8 @@
 #include <stdint.h>
 
 namespace lbmgpu {
+
+using ::fma;  // keep the float / double overloads visible beside fma(fx64, ...)
 
 constexpr int FX_SHIFT = 58;
 
@@ -78,10 +80,22 @@ __device__ __forceinline__ fx64& operator+=(fx64& a, fx64 b) {
     return a;
 }
 
+// Product with 32-bit limbs a = aH 2^32 + aL (aH signed, aL unsigned):
+//   a b 2^-58 = aH bH 2^6 + (aH bL + aL bH + hi32(aL bL)) 2^-26 + O(2^-26).
+// The middle sum is rounded to nearest once, so the product is unbiased and
+// within 1 unit of 2^-58 of the exact value (a truncating product would drift
+// the mass by ~1e-15 per step).  The middle sum cannot overflow while both
+// operands are below 8 in magnitude; LBM populations, densities, velocities
+// and the relaxation constants here all are.
 __device__ __forceinline__ fx64 operator*(fx64 a, fx64 b) {
-    const long long hi = __mul64hi(a.v, b.v);  // bits 64..127 of the signed product
-    const unsigned long long lo = (unsigned long long)a.v * (unsigned long long)b.v;
-    return fx64((long long)(((unsigned long long)hi << (64 - FX_SHIFT)) | (lo >> FX_SHIFT)), 0);
+    constexpr int SH = FX_SHIFT - 32;
+    constexpr long long HALF = 1LL << (SH - 1);
+    const int aH = (int)(a.v >> 32), bH = (int)(b.v >> 32);
+    const unsigned aL = (unsigned)a.v, bL = (unsigned)b.v;
+    const long long hh = (long long)aH * (long long)bH;
+    const long long mid = (long long)aH * (long long)bL + (long long)aL * (long long)bH +
+                          (long long)__umulhi(aL, bL);
+    return fx64((hh << (64 - FX_SHIFT)) + ((mid + HALF) >> SH), 0);
 }
 
 __device__ __forceinline__ fx64 fma(fx64 a, fx64 b, fx64 c) { return a * b + c; }

@@ -15,6 +15,8 @@
 //               cells, then their collision.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbm_launch.h"
 
 namespace lbmgpu {
@@ -91,12 +93,12 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
     int xs, ys, zs;
     shifted<Q>(b, x, y, z, -1, xs, ys, zs);
     if (cz(Q) != 0 && (zs < 0 || zs >= g.nz)) {
-        f[Q] = (C)__ldg(src + (long long)QP * g.n + idx);
+        f[Q] = PdfStore<T>::template load<C>(src + (long long)QP * g.n + idx, QP);
         return;
     }
     const int owner = owner_of(g, parts, np, gm, xs, ys, zs);
     if (!owner) {
-        f[Q] = (C)__ldg(src + (long long)Q * g.n + lin(g, xs, ys, zs));
+        f[Q] = PdfStore<T>::template load<C>(src + (long long)Q * g.n + lin(g, xs, ys, zs), Q);
         return;
     }
     const DevParticle& P = parts[owner - 1];
@@ -107,7 +109,7 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
     double v[3];
     body_velocity(g, P, xb[0], xb[1], xb[2], v[0], v[1], v[2]);
     const double vc = v[0] * cx(QP) + v[1] * cy(QP) + v[2] * cz(QP);
-    const double ftqp = ld(src + (long long)QP * g.n + idx);  // f~_qp(x)
+    const double ftqp = ld_pdf(src + (long long)QP * g.n + idx, QP);  // f~_qp(x)
     const double wr = 3.0 * wq(QP) * cp.rho0;                 // w_q / c_s^2 * rho0
     double val;
     bool cli_done = false;
@@ -120,8 +122,8 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
         if (ok) {
             const double k0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
             const double alpha = 4.0 / (1.0 + 2.0 * delta);
-            const double f2 = ld(src + (long long)QP * g.n + lin(g, x2, y2, z2));
-            const double fq = ld(src + (long long)Q * g.n + idx);
+            const double f2 = ld_pdf(src + (long long)QP * g.n + lin(g, x2, y2, z2), QP);
+            const double fq = ld_pdf(src + (long long)Q * g.n + idx, Q);
             val = ftqp + k0 * f2 - k0 * fq - alpha * wr * vc;
             cli_done = true;
         }
@@ -163,7 +165,7 @@ __device__ __forceinline__ void mem_pull(const T* __restrict__ src, const Geom& 
                                          int x, int y, int z, long long idx, C (&f)[NQ],
                                          Slots* slots, int* status) {
     Nbr b = make_nbr(g, x, y, z);
-    f[0] = (C)__ldg(src + idx);
+    f[0] = PdfStore<T>::template load<C>(src + idx, 0);
     MemPull<T, C, 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status);
 }
 
@@ -225,30 +227,57 @@ __device__ inline void psm_collide(C (&f)[NQ], const Coll<C>& k, const Coupl& cp
 // ---------------------------------------------------------------------------
 // bulk sweep: every cell outside the near-particle regions.  Tiles that no
 // region touches skip the per-cell test (block-uniform branch).
-template <typename T, typename C, bool NOSTREAM>
-__global__ void __launch_bounds__(256)
-    k_bulk(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k,
-           const DevParticle* __restrict__ parts, int np, int all_tiles) {
-    const int tX = blockIdx.x, tY = blockIdx.y, tZ = blockIdx.z;
+// Resident 256-thread blocks per SM requested for k_bulk (at most 85
+// registers per thread).
+template <typename C> struct BulkBlocks { static constexpr int value = 3; };
+
+// One tile (tX, tY, tZ) of the bulk sweep for the calling thread (tx, ty).
+template <typename T, typename C, bool NOSTREAM, int CPT>
+__device__ __forceinline__ void bulk_tile(const T* __restrict__ src, T* __restrict__ dst,
+                                          const Geom& g, const Coll<C>& k,
+                                          const DevParticle* __restrict__ parts, int np,
+                                          int all_tiles, int tX, int tY, int tZ, int tx, int ty) {
     bool near_tile = false;
     if (!all_tiles) {
         for (int s = 0; s < np && !near_tile; ++s)
             near_tile = tile_in_reg(g, parts[s].reg, tX, tY, tZ);
     }
-    const int x = tX * g.tx + threadIdx.x, y = tY * g.ty + threadIdx.y, z = tZ;
+    const int x = tX * g.tx + tx, y = tY * g.ty + ty;
     if (x >= g.nx || y >= g.ny) return;
-    if (near_tile) {
-        for (int s = 0; s < np; ++s)
-            if (cell_in_reg(g, parts[s].reg, x, y, z)) return;  // k_near's cell
+    // CPT cells per thread along z: all their loads are issued before the
+    // first collision, doubling the bytes in flight of the 32-bit sweep
+    C f[CPT][NQ];
+    bool act[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        const int z = tZ * CPT + c;
+        act[c] = z < g.nz;
+        if (act[c] && near_tile)
+            for (int s = 0; s < np; ++s)
+                if (cell_in_reg(g, parts[s].reg, x, y, z)) act[c] = false;  // k_near's cell
+        if (act[c]) {
+            const long long idx = lin(g, x, y, z);
+            if (NOSTREAM)
+                load_own(src, g, idx, f[c]);
+            else
+                pull_plain(src, g, x, y, z, idx, f[c]);
+        }
     }
-    const long long idx = lin(g, x, y, z);
-    C f[NQ];
-    if (NOSTREAM)
-        load_own(src, g, idx, f);
-    else
-        pull_plain(src, g, x, y, z, idx, f);
-    collide_fluid(f, k);
-    store_own(dst, g, idx, f);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        if (!act[c]) continue;
+        const int z = tZ * CPT + c;
+        collide_fluid(f[c], k);
+        store_own(dst, g, lin(g, x, y, z), f[c]);
+    }
+}
+
+template <typename T, typename C, bool NOSTREAM, int CPT>
+__global__ void __launch_bounds__(256, BulkBlocks<C>::value)
+    k_bulk(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k,
+           const DevParticle* __restrict__ parts, int np, int all_tiles) {
+    bulk_tile<T, C, NOSTREAM, CPT>(src, dst, g, k, parts, np, all_tiles, blockIdx.x, blockIdx.y,
+                                   blockIdx.z, threadIdx.x, threadIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,21 +288,21 @@ __global__ void __launch_bounds__(256)
 // of a lower-index particle is left to that particle's blocks.  Each block
 // writes, for every particle q, its fixed-order force/torque sum to
 // partials[((p * nblk + blk) * np + q) * 6 + c].
+// One near-kernel block: region offsets (bx, by, bzz) of particle p, whose
+// force/torque sums land in partials[((p * nblk + blk) * np + q) * 6 + c].
+// `sp` holds the particle records in shared memory; every thread of the
+// block must call this (it synchronises for the reduction).
 template <typename T, typename C, int KIND, bool NOSTREAM>
-__global__ void __launch_bounds__(256)
-    k_near(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
-           const DevParticle* __restrict__ parts, GeoMap gm, double* __restrict__ partials,
-           int* __restrict__ status, int bz) {
-    __shared__ DevParticle sp[MAX_PARTICLES];
-    __shared__ double red[8][6];
+__device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restrict__ dst,
+                                           const Geom& g, const Coll<C>& k, const Coupl& cp,
+                                           const DevParticle* sp, const GeoMap& gm,
+                                           double* __restrict__ partials, int* __restrict__ status,
+                                           int p, int bx, int by, int bzz, long long nblk,
+                                           long long blk, double (*red)[6]) {
     const int tid = threadIdx.x + NEAR_BX * (threadIdx.y + NEAR_BY * threadIdx.z);
     constexpr int nthr = NEAR_BX * NEAR_BY * NEAR_BZ;
-    for (int i = tid; i < cp.np * (int)(sizeof(DevParticle) / sizeof(double)); i += nthr)
-        reinterpret_cast<double*>(sp)[i] = reinterpret_cast<const double*>(parts)[i];
-    __syncthreads();
-    const int p = blockIdx.z / bz, bzz = blockIdx.z % bz;
     const int* R = sp[p].reg;
-    const int kx = blockIdx.x * NEAR_BX + threadIdx.x, ky = blockIdx.y * NEAR_BY + threadIdx.y,
+    const int kx = bx * NEAR_BX + threadIdx.x, ky = by * NEAR_BY + threadIdx.y,
               kz = bzz * NEAR_BZ + threadIdx.z;
     bool active = kx < R[1] && ky < R[5] && kz < R[9];
     int x = R[0] + kx, y = R[4] + ky, z = R[8] + kz;
@@ -333,8 +362,6 @@ __global__ void __launch_bounds__(256)
     }
     if (KIND == 0 || (NOSTREAM && KIND == 2)) return;
     // fixed-order reduction of this block's contribution for each particle
-    const long long nblk = (long long)gridDim.x * gridDim.y * bz;
-    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * bzz);
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr / 32;
     for (int q = 0; q < cp.np; ++q) {
 #pragma unroll
@@ -353,6 +380,31 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
+// near-particle sweep over the cell region of each particle (cells within
+// R + NEAR_HALO of the centre per axis).  Grid (bx, by, bz * np) of
+// NEAR_BX x NEAR_BY x NEAR_BZ blocks: block (bx, by, bz) of particle p covers
+// region offsets [bx*NEAR_BX, ...) etc.; a cell that also lies in the region
+// of a lower-index particle is left to that particle's blocks.
+template <typename T, typename C, int KIND, bool NOSTREAM>
+__global__ void __launch_bounds__(256)
+    k_near(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
+           const DevParticle* __restrict__ parts, GeoMap gm, double* __restrict__ partials,
+           int* __restrict__ status, int bz) {
+    __shared__ DevParticle sp[MAX_PARTICLES];
+    __shared__ double red[8][6];
+    const int tid = threadIdx.x + NEAR_BX * (threadIdx.y + NEAR_BY * threadIdx.z);
+    constexpr int nthr = NEAR_BX * NEAR_BY * NEAR_BZ;
+    for (int i = tid; i < cp.np * (int)(sizeof(DevParticle) / sizeof(double)); i += nthr)
+        reinterpret_cast<double*>(sp)[i] = reinterpret_cast<const double*>(parts)[i];
+    __syncthreads();
+    const int p = blockIdx.z / bz, bzz = blockIdx.z % bz;
+    const long long nblk = (long long)gridDim.x * gridDim.y * bz;
+    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * bzz);
+    near_block<T, C, KIND, NOSTREAM>(src, dst, g, k, cp, sp, gm, partials, status, p, blockIdx.x,
+                                     blockIdx.y, bzz, nblk, blk, red);
+}
+
+// ---------------------------------------------------------------------------
 // Per-step geometry map (computed once per global step, before the sweeps):
 // for every cell of particle p's region, MEM: the owner under the current
 // particle state (0 fluid, s+1 inside particle s, lowest s first, R6);
@@ -360,16 +412,9 @@ __global__ void __launch_bounds__(256)
 // sweeps then read these instead of re-evaluating FP64 geometry per link.
 // Grid (ceil(ex/32), ey, ez * np), 32 threads per block.
 template <int KIND>
-__global__ void __launch_bounds__(32)
-    k_map(Geom g, Coupl cp, const DevParticle* __restrict__ parts, unsigned short* __restrict__ map,
-          int ex, int ey, int ez) {
-    __shared__ DevParticle sp[MAX_PARTICLES];
-    const int nd = cp.np * (int)(sizeof(DevParticle) / sizeof(double));
-    for (int i = threadIdx.x; i < nd; i += blockDim.x)
-        reinterpret_cast<double*>(sp)[i] = reinterpret_cast<const double*>(parts)[i];
-    __syncthreads();
-    const int p = blockIdx.z / ez, kz = blockIdx.z % ez, ky = blockIdx.y;
-    const int kx = blockIdx.x * 32 + threadIdx.x;
+__device__ __forceinline__ void map_cell(const Geom& g, const Coupl& cp, const DevParticle* sp,
+                                         unsigned short* __restrict__ map, int ex, int ey, int ez,
+                                         int p, int kx, int ky, int kz) {
     const int* R = sp[p].reg;
     if (kx >= R[1] || ky >= R[5] || kz >= R[9]) return;
     int x = R[0] + kx, y = R[4] + ky, z = R[8] + kz;
@@ -381,15 +426,28 @@ __global__ void __launch_bounds__(32)
     map[(((long long)p * ez + kz) * ey + ky) * ex + kx] = (unsigned short)v;
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(32)
+    k_map(Geom g, Coupl cp, const DevParticle* __restrict__ parts, unsigned short* __restrict__ map,
+          int ex, int ey, int ez) {
+    __shared__ DevParticle sp[MAX_PARTICLES];
+    const int nd = cp.np * (int)(sizeof(DevParticle) / sizeof(double));
+    for (int i = threadIdx.x; i < nd; i += blockDim.x)
+        reinterpret_cast<double*>(sp)[i] = reinterpret_cast<const double*>(parts)[i];
+    __syncthreads();
+    map_cell<KIND>(g, cp, sp, map, ex, ey, ez, blockIdx.z / ez, blockIdx.x * 32 + threadIdx.x,
+                   blockIdx.y, blockIdx.z % ez);
+}
+
 // ---------------------------------------------------------------------------
 // fixed-order force/torque total of particle q (one block per particle):
 // F = (S_1 + ... + S_nsub) / nsub with S_k the sum, over the near-kernel
 // blocks of every particle's region, of subcycle k's partials for q.
-__global__ void __launch_bounds__(256)
-    k_finalize(int np, long long nblk, const double* __restrict__ partials, int nsub,
-               double* __restrict__ out) {
-    __shared__ double red[256][6];
-    const int q = blockIdx.x, tid = threadIdx.x;
+__device__ __forceinline__ void finalize_block(int np, long long nblk,
+                                               const double* __restrict__ partials, int nsub,
+                                               double* __restrict__ out, int q,
+                                               double (*red)[6]) {
+    const int tid = threadIdx.x;
     const long long count = (long long)np * nblk;
     double tot[6] = {0, 0, 0, 0, 0, 0};
     for (int sub = 0; sub < nsub; ++sub) {
@@ -417,17 +475,23 @@ __global__ void __launch_bounds__(256)
         for (int c = 0; c < 6; ++c) out[q * 6 + c] = tot[c] / nsub;
 }
 
+__global__ void __launch_bounds__(256)
+    k_finalize(int np, long long nblk, const double* __restrict__ partials, int nsub,
+               double* __restrict__ out) {
+    __shared__ double red[256][6];
+    finalize_block(np, nblk, partials, nsub, out, blockIdx.x, red);
+}
+
 // ---------------------------------------------------------------------------
 // explicit Euler rigid-body update over dt, gravity + buoyancy
 // (rho_p - rho0) V g; keeps the previous state in `prev`.
-__global__ void k_rigid(Geom g, DevParticle* __restrict__ parts, DevParticle* __restrict__ prev,
-                        int np, const double* __restrict__ force, double rho0, double gx,
-                        double gy, double gz, double dt, int wall_contact,
-                        int* __restrict__ status) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    DevParticle P = parts[p];
-    prev[p] = P;
+__device__ __forceinline__ void rigid_one(const Geom& g, DevParticle* __restrict__ part,
+                                          DevParticle* __restrict__ prev,
+                                          const double* __restrict__ force, double rho0, double gx,
+                                          double gy, double gz, double dt, int wall_contact,
+                                          int* __restrict__ status) {
+    DevParticle P = *part;
+    *prev = P;
     if (P.fixed == 0.0) {
         const double PI = 3.14159265358979323846;
         const double D = P.d, R = 0.5 * D;
@@ -435,10 +499,10 @@ __global__ void k_rigid(Geom g, DevParticle* __restrict__ parts, DevParticle* __
         const double m = P.rho * V, I = m * D * D / 10.0;
         const double grav[3] = {gx, gy, gz};
         double Ft[3];
-        for (int a = 0; a < 3; ++a) Ft[a] = force[p * 6 + a] + (P.rho - rho0) * V * grav[a];
+        for (int a = 0; a < 3; ++a) Ft[a] = force[a] + (P.rho - rho0) * V * grav[a];
         for (int a = 0; a < 3; ++a) P.x[a] += dt * P.u[a];
         for (int a = 0; a < 3; ++a) P.u[a] += dt * Ft[a] / m;
-        for (int a = 0; a < 3; ++a) P.w[a] += dt * force[p * 6 + 3 + a] / I;
+        for (int a = 0; a < 3; ++a) P.w[a] += dt * force[3 + a] / I;
         const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
         for (int a = 0; a < 3; ++a) {
             if (a == 2 && g.bc_z) continue;
@@ -461,7 +525,18 @@ __global__ void k_rigid(Geom g, DevParticle* __restrict__ parts, DevParticle* __
         }
     }
     store_region(g, P);
-    parts[p] = P;
+    *part = P;
+}
+
+// explicit Euler rigid-body update over dt, gravity + buoyancy
+// (rho_p - rho0) V g; keeps the previous state in `prev`.
+__global__ void k_rigid(Geom g, DevParticle* __restrict__ parts, DevParticle* __restrict__ prev,
+                        int np, const double* __restrict__ force, double rho0, double gx,
+                        double gy, double gz, double dt, int wall_contact,
+                        int* __restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    rigid_one(g, parts + p, prev + p, force + 6 * p, rho0, gx, gy, gz, dt, wall_contact, status);
 }
 
 __global__ void k_regions(Geom g, DevParticle* parts, int np) {
@@ -481,20 +556,11 @@ __global__ void k_regions(Geom g, DevParticle* parts, int np) {
 //   extrapolate = 0: f_eq(rho0, v);
 // and is then collided (plain fluid collision) into dst.
 template <typename T, typename C>
-__global__ void __launch_bounds__(128)
-    k_refill(const T* __restrict__ srcB, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
-             const DevParticle* __restrict__ p_old, const DevParticle* __restrict__ p_new,
-             int extrapolate, int side, int* __restrict__ status) {
-    __shared__ DevParticle so[MAX_PARTICLES], sn[MAX_PARTICLES];
-    const int tid = threadIdx.x;
-    const int nd = cp.np * (int)(sizeof(DevParticle) / sizeof(double));
-    for (int i = tid; i < nd; i += blockDim.x) {
-        reinterpret_cast<double*>(so)[i] = reinterpret_cast<const double*>(p_old)[i];
-        reinterpret_cast<double*>(sn)[i] = reinterpret_cast<const double*>(p_new)[i];
-    }
-    __syncthreads();
-    const int p = blockIdx.y;
-    const long long lid = (long long)blockIdx.x * blockDim.x + tid;
+__device__ __forceinline__ void refill_cell(const T* __restrict__ srcB, T* __restrict__ dst,
+                                            const Geom& g, const Coll<C>& k, const Coupl& cp,
+                                            const DevParticle* so, const DevParticle* sn,
+                                            int extrapolate, int side, int p, long long lid,
+                                            int* __restrict__ status) {
     if (lid >= (long long)side * side * side) return;
     const int kx = (int)(lid % side), ky = (int)((lid / side) % side),
               kz = (int)(lid / ((long long)side * side));
@@ -616,6 +682,23 @@ __global__ void __launch_bounds__(128)
     store_own(dst, g, lin(g, x, y, z), fn);
 }
 
+template <typename T, typename C>
+__global__ void __launch_bounds__(128)
+    k_refill(const T* __restrict__ srcB, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
+             const DevParticle* __restrict__ p_old, const DevParticle* __restrict__ p_new,
+             int extrapolate, int side, int* __restrict__ status) {
+    __shared__ DevParticle so[MAX_PARTICLES], sn[MAX_PARTICLES];
+    const int tid = threadIdx.x;
+    const int nd = cp.np * (int)(sizeof(DevParticle) / sizeof(double));
+    for (int i = tid; i < nd; i += blockDim.x) {
+        reinterpret_cast<double*>(so)[i] = reinterpret_cast<const double*>(p_old)[i];
+        reinterpret_cast<double*>(sn)[i] = reinterpret_cast<const double*>(p_new)[i];
+    }
+    __syncthreads();
+    refill_cell<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, side, blockIdx.y,
+                      (long long)blockIdx.x * blockDim.x + tid, status);
+}
+
 // ---------------------------------------------------------------------------
 // macroscopic fields of the pre-collision state at the start of the next step
 // what: 2 rho, 3 u, 4 eps (PSM), 5 owner flag (MEM)
@@ -647,7 +730,7 @@ __global__ void __launch_bounds__(256)
             // post-collision moments: rho is conserved, j gains f_ext
             double r = 0.0, j[3] = {0.0, 0.0, 0.0};
             for (int q = 0; q < NQ; ++q) {
-                double v = ld(state + (long long)q * g.n + i);
+                double v = ld_pdf(state + (long long)q * g.n + i, q);
                 r += v;
                 j[0] += v * cx(q);
                 j[1] += v * cy(q);
@@ -720,13 +803,199 @@ __global__ void k_init_eq(T* __restrict__ dst, Geom g, double rho, double ux, do
     double e[NQ];
     equilibrium(rho, ux, uy, uz, rho0, e);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + i] = (T)e[q];
+    for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + i] = PdfStore<T>::template save<double>(e[q], q);
 }
 
 template <typename T>
-__global__ void k_from_f64(const double* __restrict__ in, T* __restrict__ out, long long count) {
+__global__ void k_to_f64(const T* __restrict__ in, double* __restrict__ out, long long count,
+                         long long ncell) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) out[i] = (T)in[i];
+    if (i < count) out[i] = ld_pdf(in + i, (int)(i / ncell));
+}
+
+template <typename T>
+__global__ void k_from_f64(const double* __restrict__ in, T* __restrict__ out, long long count,
+                           long long ncell) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = PdfStore<T>::template save<double>(in[i], (int)(i / ncell));
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched ensemble kernels.  Each launch covers every case of a work list;
+// block (or work item) t belongs to case list[i] with base[i] <= t < base[i+1].
+__device__ __forceinline__ int find_item(const long long* __restrict__ base, int n, long long t) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(base + mid) <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename C>
+__device__ __forceinline__ const Coll<C>& batch_coll(const BatchCase& B);
+template <>
+__device__ __forceinline__ const Coll<double>& batch_coll<double>(const BatchCase& B) {
+    return B.kd;
+}
+template <>
+__device__ __forceinline__ const Coll<fx64>& batch_coll<fx64>(const BatchCase& B) {
+    return B.kfx;
+}
+
+// cell and tile ranges of each case's particle (after upload or a change of
+// the bulk tiling); the previous state starts equal to the current one
+__global__ void k_batch_regions(BatchCase* __restrict__ cases, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    store_region(cases[c].g, *cases[c].part);
+    *cases[c].prev = *cases[c].part;
+}
+
+// f = f_eq(rho0, 0) in the stored buffer of every case (fluid at rest: the
+// post-collision and pre-collision fields coincide).
+__global__ void k_batch_init(BatchCase* __restrict__ cases) {
+    const BatchCase& B = cases[blockIdx.y];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.g.n) return;
+    double e[NQ];
+    equilibrium(B.kd.rho0, 0.0, 0.0, 0.0, B.kd.rho0, e);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) B.buf[B.cur][(long long)q * B.g.n + i] = e[q];
+}
+
+// geometry map: 32-thread blocks over (x chunk, y, z) of each case's region
+__global__ void __launch_bounds__(32) k_batch_map(BatchCase* __restrict__ cases, BatchList l) {
+    __shared__ DevParticle sp[1];
+    const int i = find_item(l.base, l.n, blockIdx.x);
+    const BatchCase& B = cases[l.list[i]];
+    const long long local = blockIdx.x - l.base[i];
+    for (int k = threadIdx.x; k < (int)(sizeof(DevParticle) / sizeof(double)); k += 32)
+        reinterpret_cast<double*>(sp)[k] = reinterpret_cast<const double*>(B.part)[k];
+    __syncthreads();
+    const int nbx = (B.map_ext[0] + 31) / 32;
+    const int bx = (int)(local % nbx);
+    const long long rest = local / nbx;
+    const int ky = (int)(rest % B.map_ext[1]), kz = (int)(rest / B.map_ext[1]);
+    if (B.kind == 2)
+        map_cell<2>(B.g, B.cp, sp, B.map, B.map_ext[0], B.map_ext[1], B.map_ext[2], 0,
+                    bx * 32 + threadIdx.x, ky, kz);
+    else
+        map_cell<1>(B.g, B.cp, sp, B.map, B.map_ext[0], B.map_ext[1], B.map_ext[2], 0,
+                    bx * 32 + threadIdx.x, ky, kz);
+}
+
+// near-particle sweep: one near block of one case per thread block
+__global__ void __launch_bounds__(256)
+    k_batch_near(BatchCase* __restrict__ cases, BatchList l, int sub, int* __restrict__ status) {
+    __shared__ DevParticle sp[1];
+    __shared__ double red[8][6];
+    const int i = find_item(l.base, l.n, blockIdx.x);
+    const BatchCase& B = cases[l.list[i]];
+    const long long local = blockIdx.x - l.base[i];
+    const int tid = threadIdx.x + NEAR_BX * (threadIdx.y + NEAR_BY * threadIdx.z);
+    for (int k = tid; k < (int)(sizeof(DevParticle) / sizeof(double)); k += NEAR_BX * NEAR_BY * NEAR_BZ)
+        reinterpret_cast<double*>(sp)[k] = reinterpret_cast<const double*>(B.part)[k];
+    __syncthreads();
+    const int bx = (int)(local % B.box[0]);
+    const int by = (int)((local / B.box[0]) % B.box[1]);
+    const int bzz = (int)(local / ((long long)B.box[0] * B.box[1]));
+    const GeoMap gm{B.map, B.map_ext[0], B.map_ext[1], B.map_ext[2]};
+    const int cur = B.cur;
+    double* partials = B.partials + (long long)sub * B.nblk * 6;
+    if (B.kind == 2)
+        near_block<double, double, 2, false>(B.buf[cur], B.buf[1 - cur], B.g, B.kd, B.cp, sp, gm,
+                                             partials, status, 0, bx, by, bzz, B.nblk, local, red);
+    else
+        near_block<double, double, 1, false>(B.buf[cur], B.buf[1 - cur], B.g, B.kd, B.cp, sp, gm,
+                                             partials, status, 0, bx, by, bzz, B.nblk, local, red);
+}
+
+// One 256-cell segment of an xy plane of the bulk sweep: cells
+// l = seg * 256 + t (x fastest) of plane z.  Domains whose nx is not a
+// multiple of the warp width keep every lane busy (box tiles of tx cells
+// leave tx - nx mod tx lanes of each row idle).
+template <typename C>
+__device__ __forceinline__ void bulk_segment(const double* __restrict__ src,
+                                             double* __restrict__ dst, const Geom& g,
+                                             const Coll<C>& k, const int* reg, int seg, int z,
+                                             int t) {
+    const int l = seg * 256 + t;
+    if (l >= g.nx * g.ny) return;
+    const int y = l / g.nx, x = l - y * g.nx;
+    if (cell_in_reg(g, reg, x, y, z)) return;  // k_batch_near's cell
+    const long long idx = lin(g, x, y, z);
+    C f[NQ];
+    pull_plain(src, g, x, y, z, idx, f);
+    collide_fluid(f, k);
+    store_own(dst, g, idx, f);
+}
+
+// bulk sweep: persistent 256-thread blocks striding over the tiles of all
+// listed cases.  LAYOUT 0: box tiles of the case's g.tx x g.ty cells (thread
+// t -> (t mod g.tx, t / g.tx)); LAYOUT 1: 256-cell plane segments.
+template <typename C, int LAYOUT>
+__global__ void __launch_bounds__(256, BulkBlocks<C>::value)
+    k_batch_bulk(BatchCase* __restrict__ cases, BatchList l, long long total) {
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int i = find_item(l.base, l.n, t);
+        const BatchCase& B = cases[l.list[i]];
+        const long long local = t - l.base[i];
+        const int cur = B.cur;
+        if (LAYOUT == 1) {
+            const int nseg = (B.g.nx * B.g.ny + 255) / 256;
+            bulk_segment<C>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B), B.part->reg,
+                            (int)(local % nseg), (int)(local / nseg), threadIdx.x);
+        } else {
+            const int tX = (int)(local % B.g.ntx);
+            const int tY = (int)((local / B.g.ntx) % B.g.nty);
+            const int tZ = (int)(local / ((long long)B.g.ntx * B.g.nty));
+            bulk_tile<double, C, false, 1>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B),
+                                           B.part, 1, 0, tX, tY, tZ, threadIdx.x % B.g.tx,
+                                           threadIdx.x / B.g.tx);
+        }
+    }
+}
+
+__global__ void k_batch_swap(BatchCase* __restrict__ cases, BatchList l) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < l.n) cases[l.list[i]].cur ^= 1;
+}
+
+__global__ void __launch_bounds__(256) k_batch_finalize(BatchCase* __restrict__ cases) {
+    __shared__ double red[256][6];
+    const BatchCase& B = cases[blockIdx.x];
+    const int nsub = B.kind == 2 ? B.subcycles : 1;
+    finalize_block(1, B.nblk, B.partials, nsub, B.force, 0, red);
+}
+
+__global__ void k_batch_rigid(BatchCase* __restrict__ cases, int n, int* __restrict__ status) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const BatchCase& B = cases[c];
+    const double dt = B.kind == 2 ? (double)B.subcycles : 1.0;
+    rigid_one(B.g, B.part, B.prev, B.force, B.kd.rho0, B.gravity[0], B.gravity[1], B.gravity[2],
+              dt, B.wall_contact, status);
+}
+
+// MEM re-mapping and refilling after the step (reads the buffer the last
+// sweep pulled from, writes the stored state)
+__global__ void __launch_bounds__(128)
+    k_batch_refill(BatchCase* __restrict__ cases, BatchList l, int* __restrict__ status) {
+    __shared__ DevParticle so[1], sn[1];
+    const int i = find_item(l.base, l.n, blockIdx.x);
+    const BatchCase& B = cases[l.list[i]];
+    const long long local = blockIdx.x - l.base[i];
+    for (int k = threadIdx.x; k < (int)(sizeof(DevParticle) / sizeof(double)); k += blockDim.x) {
+        reinterpret_cast<double*>(so)[k] = reinterpret_cast<const double*>(B.prev)[k];
+        reinterpret_cast<double*>(sn)[k] = reinterpret_cast<const double*>(B.part)[k];
+    }
+    __syncthreads();
+    const int cur = B.cur;
+    refill_cell<double, double>(B.buf[1 - cur], B.buf[cur], B.g, B.kd, B.cp, so, sn, 1,
+                                B.refill_side, 0, local * blockDim.x + threadIdx.x, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -751,30 +1020,41 @@ const Coll<fx64>& coll_of<double, fx64>(const Launch& L) {
     return L.kfx;
 }
 
+template <typename T, typename C, int CPT>
+cudaError_t bulk_cpt(const void* src, void* dst, const Launch& L) {
+    dim3 grid(L.g.ntx, L.g.nty, L.g.ntz);
+    const auto& k = coll_of<typename std::conditional<(sizeof(T) < 4), C, T>::type, C>(L);
+    if (L.nostream)
+        k_bulk<T, C, true, CPT><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
+                                                                L.parts, L.cp.np, L.all_tiles);
+    else
+        k_bulk<T, C, false, CPT><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
+                                                                 L.parts, L.cp.np, L.all_tiles);
+    return cudaGetLastError();
+}
+
+// FP64-state sweeps are arithmetic bound and use one cell per thread; the
+// 16/32-bit sweeps are memory bound and take two z cells per thread.
 template <typename T, typename C = T>
 cudaError_t bulk_t(const void* src, void* dst, const Launch& L) {
-    dim3 grid(L.g.ntx, L.g.nty, L.g.ntz);
-    const auto& k = coll_of<T, C>(L);
-    if (L.nostream)
-        k_bulk<T, C, true><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k, L.parts,
-                                                           L.cp.np, L.all_tiles);
-    else
-        k_bulk<T, C, false><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
-                                                            L.parts, L.cp.np, L.all_tiles);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) <= 4) {
+        if (L.g.tz == 2) return bulk_cpt<T, C, 2>(src, dst, L);
+    }
+    return bulk_cpt<T, C, 1>(src, dst, L);
 }
 
 template <typename T, int KIND>
 cudaError_t near_kind(const void* src, void* dst, const Launch& L) {
+    using C = typename ComputeOf<T>::type;
     dim3 grid(L.box[0], L.box[1], L.box[2] * L.cp.np);
     dim3 block(NEAR_BX, NEAR_BY, NEAR_BZ);
-    const auto& k = coll_of<T, T>(L);
+    const auto& k = coll_of<C, C>(L);
     const GeoMap gm{L.map, L.map_ext[0], L.map_ext[1], L.map_ext[2]};
     if (L.nostream)
-        k_near<T, T, KIND, true><<<grid, block, 0, L.stream>>>(
+        k_near<T, C, KIND, true><<<grid, block, 0, L.stream>>>(
             (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, gm, L.partials, L.status, L.box[2]);
     else
-        k_near<T, T, KIND, false><<<grid, block, 0, L.stream>>>(
+        k_near<T, C, KIND, false><<<grid, block, 0, L.stream>>>(
             (const T*)src, (T*)dst, L.g, k, L.cp, L.parts, gm, L.partials, L.status, L.box[2]);
     return cudaGetLastError();
 }
@@ -790,69 +1070,120 @@ cudaError_t near_t(const void* src, void* dst, const Launch& L) {
 template <typename T>
 cudaError_t refill_t(const void* srcB, void* dst, const Launch& L, const DevParticle* po,
                      const DevParticle* pn, int extrapolate) {
+    using C = typename ComputeOf<T>::type;
     if (L.cp.np <= 0) return cudaSuccess;
     int side = L.box[0];  // set by the caller: cube side in cells
     long long cells = (long long)side * side * side;
     dim3 grid((unsigned)((cells + 127) / 128), L.cp.np, 1);
-    k_refill<T, T><<<grid, 128, 0, L.stream>>>((const T*)srcB, (T*)dst, L.g, coll_of<T, T>(L),
+    k_refill<T, C><<<grid, 128, 0, L.stream>>>((const T*)srcB, (T*)dst, L.g, coll_of<C, C>(L),
                                                 L.cp, po, pn, extrapolate, side, L.status);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t macro_t(const void* state, const Launch& L, int what, void* out) {
+    using C = typename ComputeOf<T>::type;
     unsigned blocks = (unsigned)((L.g.n + 255) / 256);
-    const auto& k = coll_of<T, T>(L);
-    double fx = (double)k.fx, fy = (double)k.fy, fz = (double)k.fz;
-    if (sizeof(T) == 8) {
-        fx = L.kd.fx;
-        fy = L.kd.fy;
-        fz = L.kd.fz;
-    }
+    const auto& k = coll_of<C, C>(L);
+    const double fx = L.kd.fx, fy = L.kd.fy, fz = L.kd.fz;
     if (L.nostream)
-        k_macro<T, T, true><<<blocks, 256, 0, L.stream>>>((const T*)state, L.g, k, L.cp, L.parts,
+        k_macro<T, C, true><<<blocks, 256, 0, L.stream>>>((const T*)state, L.g, k, L.cp, L.parts,
                                                           fx, fy, fz, what, out);
     else
-        k_macro<T, T, false><<<blocks, 256, 0, L.stream>>>((const T*)state, L.g, k, L.cp, L.parts,
+        k_macro<T, C, false><<<blocks, 256, 0, L.stream>>>((const T*)state, L.g, k, L.cp, L.parts,
                                                            fx, fy, fz, what, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t init_eq_t(void* dst, const Launch& L, double rho, double ux, double uy, double uz) {
+    unsigned blocks = (unsigned)((L.g.n + 255) / 256);
+    k_init_eq<T><<<blocks, 256, 0, L.stream>>>((T*)dst, L.g, rho, ux, uy, uz, L.kd.rho0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t to_f64_t(const void* in, double* out, long long count, long long ncell,
+                     cudaStream_t s) {
+    unsigned blocks = (unsigned)((count + 255) / 256);
+    k_to_f64<T><<<blocks, 256, 0, s>>>((const T*)in, out, count, ncell);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t from_f64_t(const double* in, void* dst, long long count, long long ncell,
+                       cudaStream_t s) {
+    unsigned blocks = (unsigned)((count + 255) / 256);
+    k_from_f64<T><<<blocks, 256, 0, s>>>(in, (T*)dst, count, ncell);
     return cudaGetLastError();
 }
 }  // namespace
 
+// storage codes: ST_F64 0, ST_F32 1, ST_F16 4, ST_BF16 5 (FP64 is also the
+// state of the float-float (2) and fixed-point (3) bulk modes)
 cudaError_t launch_bulk(int storage, const void* src, void* dst, const Launch& L) {
-    if (storage == 2) return bulk_t<double, dfloat>(src, dst, L);
-    if (storage == 3) return bulk_t<double, fx64>(src, dst, L);
-    return storage == 0 ? bulk_t<double>(src, dst, L) : bulk_t<float>(src, dst, L);
+    switch (storage) {
+        case 2: return bulk_t<double, dfloat>(src, dst, L);
+        case 3: return bulk_t<double, fx64>(src, dst, L);
+        case 1: return bulk_t<float>(src, dst, L);
+        case 4: return bulk_t<__half, float>(src, dst, L);
+        case 5: return bulk_t<__nv_bfloat16, float>(src, dst, L);
+        default: return bulk_t<double>(src, dst, L);
+    }
 }
 cudaError_t launch_near(int storage, const void* src, void* dst, const Launch& L) {
-    return storage == 0 ? near_t<double>(src, dst, L) : near_t<float>(src, dst, L);
+    switch (storage) {
+        case 1: return near_t<float>(src, dst, L);
+        case 4: return near_t<__half>(src, dst, L);
+        case 5: return near_t<__nv_bfloat16>(src, dst, L);
+        default: return near_t<double>(src, dst, L);
+    }
 }
 cudaError_t launch_refill(int storage, const void* srcB, void* dst, const Launch& L,
                           const DevParticle* p_old, const DevParticle* p_new, int extrapolate) {
-    return storage == 0 ? refill_t<double>(srcB, dst, L, p_old, p_new, extrapolate)
-                        : refill_t<float>(srcB, dst, L, p_old, p_new, extrapolate);
+    switch (storage) {
+        case 1: return refill_t<float>(srcB, dst, L, p_old, p_new, extrapolate);
+        case 4: return refill_t<__half>(srcB, dst, L, p_old, p_new, extrapolate);
+        case 5: return refill_t<__nv_bfloat16>(srcB, dst, L, p_old, p_new, extrapolate);
+        default: return refill_t<double>(srcB, dst, L, p_old, p_new, extrapolate);
+    }
 }
 cudaError_t launch_macro(int storage, const void* state, const Launch& L, int what, void* out) {
-    return storage == 0 ? macro_t<double>(state, L, what, out) : macro_t<float>(state, L, what, out);
+    switch (storage) {
+        case 1: return macro_t<float>(state, L, what, out);
+        case 4: return macro_t<__half>(state, L, what, out);
+        case 5: return macro_t<__nv_bfloat16>(state, L, what, out);
+        default: return macro_t<double>(state, L, what, out);
+    }
 }
 cudaError_t launch_init_eq(int storage, void* dst, const Launch& L, double rho, double ux,
                            double uy, double uz) {
-    unsigned blocks = (unsigned)((L.g.n + 255) / 256);
-    if (storage == 0)
-        k_init_eq<double><<<blocks, 256, 0, L.stream>>>((double*)dst, L.g, rho, ux, uy, uz,
-                                                        L.kd.rho0);
-    else
-        k_init_eq<float><<<blocks, 256, 0, L.stream>>>((float*)dst, L.g, rho, ux, uy, uz,
-                                                       L.kd.rho0);
-    return cudaGetLastError();
+    switch (storage) {
+        case 1: return init_eq_t<float>(dst, L, rho, ux, uy, uz);
+        case 4: return init_eq_t<__half>(dst, L, rho, ux, uy, uz);
+        case 5: return init_eq_t<__nv_bfloat16>(dst, L, rho, ux, uy, uz);
+        default: return init_eq_t<double>(dst, L, rho, ux, uy, uz);
+    }
+}
+cudaError_t launch_to_f64(int storage, const void* in, double* out, long long count,
+                          long long ncell, cudaStream_t s) {
+    switch (storage) {
+        case 1: return to_f64_t<float>(in, out, count, ncell, s);
+        case 4: return to_f64_t<__half>(in, out, count, ncell, s);
+        case 5: return to_f64_t<__nv_bfloat16>(in, out, count, ncell, s);
+        default:
+            return cudaMemcpyAsync(out, in, sizeof(double) * count, cudaMemcpyDeviceToDevice, s);
+    }
 }
 cudaError_t launch_from_f64(int storage, const double* in, void* dst, long long count,
-                            cudaStream_t s) {
-    unsigned blocks = (unsigned)((count + 255) / 256);
-    if (storage == 0)
-        return cudaMemcpyAsync(dst, in, sizeof(double) * count, cudaMemcpyDeviceToDevice, s);
-    k_from_f64<float><<<blocks, 256, 0, s>>>(in, (float*)dst, count);
-    return cudaGetLastError();
+                            long long ncell, cudaStream_t s) {
+    switch (storage) {
+        case 1: return from_f64_t<float>(in, dst, count, ncell, s);
+        case 4: return from_f64_t<__half>(in, dst, count, ncell, s);
+        case 5: return from_f64_t<__nv_bfloat16>(in, dst, count, ncell, s);
+        default:
+            return cudaMemcpyAsync(dst, in, sizeof(double) * count, cudaMemcpyDeviceToDevice, s);
+    }
 }
 cudaError_t launch_map(const Launch& L) {
     if (L.cp.np <= 0 || L.cp.kind == 0) return cudaSuccess;
@@ -883,6 +1214,68 @@ cudaError_t launch_regions(const Launch& L) {
     if (L.cp.np <= 0) return cudaSuccess;
     k_regions<<<1, 32, 0, L.stream>>>(L.g, L.parts, L.cp.np);
     return cudaGetLastError();
+}
+
+
+cudaError_t launch_batch_regions(BatchCase* cases, int n, cudaStream_t s) {
+    k_batch_regions<<<(n + 63) / 64, 64, 0, s>>>(cases, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_init(BatchCase* cases, int n, long long max_cells, cudaStream_t s) {
+    dim3 grid((unsigned)((max_cells + 255) / 256), n, 1);
+    k_batch_init<<<grid, 256, 0, s>>>(cases);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_map(BatchCase* cases, BatchList l, long long total, cudaStream_t s) {
+    if (l.n == 0 || total == 0) return cudaSuccess;
+    k_batch_map<<<(unsigned)total, 32, 0, s>>>(cases, l);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_near(BatchCase* cases, BatchList l, long long total, int sub,
+                              int* status, cudaStream_t s) {
+    if (l.n == 0 || total == 0) return cudaSuccess;
+    k_batch_near<<<(unsigned)total, dim3(NEAR_BX, NEAR_BY, NEAR_BZ), 0, s>>>(cases, l, sub, status);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_bulk(int mode, int layout, BatchCase* cases, BatchList l,
+                              long long total, int grid, cudaStream_t s) {
+    if (l.n == 0 || total == 0) return cudaSuccess;
+    const unsigned gsz = (unsigned)(grid <= 0 || total < grid ? total : grid);
+    if (mode == 3) {
+        if (layout == 1) k_batch_bulk<fx64, 1><<<gsz, 256, 0, s>>>(cases, l, total);
+        else k_batch_bulk<fx64, 0><<<gsz, 256, 0, s>>>(cases, l, total);
+    } else {
+        if (layout == 1) k_batch_bulk<double, 1><<<gsz, 256, 0, s>>>(cases, l, total);
+        else k_batch_bulk<double, 0><<<gsz, 256, 0, s>>>(cases, l, total);
+    }
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s) {
+    if (l.n == 0) return cudaSuccess;
+    k_batch_swap<<<(l.n + 63) / 64, 64, 0, s>>>(cases, l);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_finalize(BatchCase* cases, int n, cudaStream_t s) {
+    k_batch_finalize<<<n, 256, 0, s>>>(cases);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_t s) {
+    k_batch_rigid<<<(n + 63) / 64, 64, 0, s>>>(cases, n, status);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, int* status,
+                                cudaStream_t s) {
+    if (l.n == 0 || total == 0) return cudaSuccess;
+    k_batch_refill<<<(unsigned)total, 128, 0, s>>>(cases, l, status);
+    return cudaGetLastError();
+}
+int batch_bulk_blocks_per_sm(int mode) {
+    int nb = 0;
+    if (mode == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<fx64, 0>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<double, 0>, 256, 0);
+    return nb > 0 ? nb : 1;
 }
 
 }  // namespace lbmgpu

@@ -65,6 +65,72 @@ inline long long near_partial_doubles(const int box[3], int np) {
     return n * near_blocks(box) * n * 6;
 }
 
+// ---- batched ensemble ----------------------------------------------------------
+// One independent simulation of a batch (one particle, FP64 PDFs).  Lives in
+// device memory; the kernels read buf[cur] and flip cur themselves, so one
+// step's launches are the same every step and can be replayed as a graph.
+struct BatchCase {
+    Geom g;
+    double* buf[2];
+    int cur;
+    int kind;          // 1 PSM, 2 MEM, 0 none
+    int subcycles;     // LBM sweeps per global step
+    int wall_contact;
+    Coupl cp;          // np = 1
+    Coll<double> kd;
+    Coll<fx64> kfx;
+    DevParticle* part;
+    DevParticle* prev;
+    double* force;     // 6 doubles
+    double* partials;  // subcycles x nblk x 6
+    unsigned short* map;
+    int map_ext[3];
+    int box[3];        // near-kernel grid (blocks)
+    long long nblk;
+    int refill_side;
+    double gravity[3];
+};
+
+// Work list of a batched launch: cases list[0..n) with prefix sums base[] of
+// their work items (tiles, blocks or cells).
+struct BatchList {
+    const int* list;
+    const long long* base;  // n + 1 entries
+    int n;
+};
+
+// Collision constants of Eq. (5) / (9)-(11) with the forcing of Eq. (7)
+// (computed in FP64, rounded once to C).
+template <typename C>
+inline Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) {
+    Coll<C> k{};
+    k.lam_p = (C)lp;
+    k.lam_m = (C)lm;
+    k.rho0 = (C)rho0;
+    k.inv_rho0 = (C)(1.0 / rho0);
+    k.fx = (C)fe[0];
+    k.fy = (C)fe[1];
+    k.fz = (C)fe[2];
+    k.has_force = (fe[0] != 0.0 || fe[1] != 0.0 || fe[2] != 0.0);
+    k.alpha = (C)(1.0 + 0.5 * (lp + lm));
+    k.beta = (C)(0.5 * (lp - lm));
+    k.c0 = (C)(1.0 + lp);
+    k.m15r0 = (C)(-1.5 * rho0);
+    const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    for (int c = 0; c < 3; ++c) {
+        k.lpw[c] = (C)(lp * w[c]);
+        k.k1w[c] = (C)(4.5 * lp * w[c] * rho0);
+        k.k2w[c] = (C)(3.0 * lm * w[c] * rho0);
+        k.hw[c] = (C)(3.0 * w[c]);
+    }
+    for (int q = 1; q < NQ; q += 2) {
+        const double cf = cx(q) * fe[0] + cy(q) * fe[1] + cz(q) * fe[2];
+        k.gq[(q - 1) / 2] = (C)(9.0 * wq(q) * cf);
+        k.fq[(q - 1) / 2] = (C)(3.0 * wq(q) * cf);
+    }
+    return k;
+}
+
 // Status bits raised by kernels (OR-ed into *status).
 enum : int {
     ST_TOO_MANY_OBJECTS = 1,  // more than CELL_SLOTS particles touch a cell
@@ -72,9 +138,10 @@ enum : int {
     ST_REFILL_SOLID = 4,      // refill found no particle owning a cell (internal)
 };
 
-// storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision);
-// launch_bulk also takes 2 = FP64 storage with float-float collision and
-// 3 = FP64 storage with 64-bit fixed-point collision
+// storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision), 4 = FP16
+// and 5 = BF16 shifted populations f - w_q (FP32 arithmetic); launch_bulk
+// also takes 2 = FP64 storage with float-float collision and 3 = FP64
+// storage with 64-bit fixed-point collision
 cudaError_t launch_bulk(int storage, const void* src, void* dst, const Launch& L);
 cudaError_t launch_near(int storage, const void* src, void* dst, const Launch& L);
 cudaError_t launch_refill(int storage, const void* srcB, void* dst, const Launch& L,
@@ -83,9 +150,27 @@ cudaError_t launch_macro(int storage, const void* state, const Launch& L, int wh
 cudaError_t launch_init_eq(int storage, void* dst, const Launch& L, double rho, double ux,
                            double uy, double uz);
 cudaError_t launch_from_f64(int storage, const double* in, void* dst, long long count,
-                            cudaStream_t s);
+                            long long ncell, cudaStream_t s);
+cudaError_t launch_to_f64(int storage, const void* in, double* out, long long count,
+                          long long ncell, cudaStream_t s);
 cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out);
 cudaError_t launch_regions(const Launch& L);
+// batched ensemble (all cases on one stream; see lbm_batch.cu)
+cudaError_t launch_batch_regions(BatchCase* cases, int n, cudaStream_t s);
+cudaError_t launch_batch_map(BatchCase* cases, BatchList l, long long total, cudaStream_t s);
+cudaError_t launch_batch_near(BatchCase* cases, BatchList l, long long total, int sub,
+                              int* status, cudaStream_t s);
+// mode 0 FP64 / 3 fixed-point collision; layout 0 box tiles (case's g.tx),
+// 1 plane segments; grid <= 0: one block per tile
+cudaError_t launch_batch_bulk(int mode, int layout, BatchCase* cases, BatchList l,
+                              long long total, int grid, cudaStream_t s);
+cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s);
+cudaError_t launch_batch_finalize(BatchCase* cases, int n, cudaStream_t s);
+cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_t s);
+cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, int* status,
+                                cudaStream_t s);
+cudaError_t launch_batch_init(BatchCase* cases, int n, long long max_cells, cudaStream_t s);
+int batch_bulk_blocks_per_sm(int mode);
 cudaError_t launch_map(const Launch& L);
 cudaError_t launch_rigid_body(const Launch& L, const double* force, double gx, double gy,
                               double gz, double dt, int wall_contact);

@@ -112,6 +112,7 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     g.ty = 256 / g.tx;
     g.ntx = (cfg->nx + g.tx - 1) / g.tx;
     g.nty = (cfg->ny + g.ty - 1) / g.ty;
+    g.tz = 1;
     g.ntz = cfg->nz;
     double maxd = 0.0;
     DevParticle recs[MAX_PARTICLES];
@@ -180,36 +181,7 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     const double lp = -1.0 / cfg->tau;
     const double lm =
         cfg->collision == LBM_TRT ? 1.0 / (cfg->magic / (0.5 + 1.0 / lp) - 0.5) : lp;
-    L.kd = Coll<double>{};
-    {
-        // same constants as the handle path
-        Coll<double>& k = L.kd;
-        const double* fe = cfg->force_density;
-        k.lam_p = lp;
-        k.lam_m = lm;
-        k.rho0 = cfg->rho0;
-        k.inv_rho0 = 1.0 / cfg->rho0;
-        k.fx = fe[0];
-        k.fy = fe[1];
-        k.fz = fe[2];
-        k.has_force = (fe[0] != 0.0 || fe[1] != 0.0 || fe[2] != 0.0);
-        k.alpha = 1.0 + 0.5 * (lp + lm);
-        k.beta = 0.5 * (lp - lm);
-        k.c0 = 1.0 + lp;
-        k.m15r0 = -1.5 * cfg->rho0;
-        const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
-        for (int c = 0; c < 3; ++c) {
-            k.lpw[c] = lp * w[c];
-            k.k1w[c] = 4.5 * lp * w[c] * cfg->rho0;
-            k.k2w[c] = 3.0 * lm * w[c] * cfg->rho0;
-            k.hw[c] = 3.0 * w[c];
-        }
-        for (int q = 1; q < NQ; q += 2) {
-            const double cf = cx(q) * fe[0] + cy(q) * fe[1] + cz(q) * fe[2];
-            k.gq[(q - 1) / 2] = 9.0 * wq(q) * cf;
-            k.fq[(q - 1) / 2] = 3.0 * wq(q) * cf;
-        }
-    }
+    L.kd = make_coll<double>(lp, lm, cfg->rho0, cfg->force_density);
     const bool psm = cfg->coupling <= LBM_PSM_M3B2;
     L.cp.kind = !coupled ? 0 : (psm ? 1 : 2);
     L.cp.variant = psm ? cfg->coupling - LBM_PSM_M1B1 : cfg->coupling - LBM_MEM_BB;

@@ -91,3 +91,14 @@ def test_enum_values_match_header():
         assert re.search(rf"LBM_{name}\s*=\s*{val}\b", text), name
     for st, name in binding.STATUS_NAMES.items():
         assert re.search(rf"{name}\s*=\s*{st}\b", text), name
+
+
+def test_binding_wrapper_surface():
+    """The Python wrapper keeps the methods the tests and the benchmark use."""
+    for name in ("set_particles", "get_particles", "init_equilibrium", "step", "forces",
+                 "set_pdf_pre", "pdf", "pdf_f64", "set_pdf", "macro", "eps", "flags",
+                 "synchronize", "close"):
+        assert callable(getattr(binding.Simulation, name)), name
+    for name in binding.EXPORTED:
+        if name not in ("lbm_last_error", "lbm_abi_version"):
+            assert callable(getattr(binding, name)), name

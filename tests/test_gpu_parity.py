@@ -52,7 +52,7 @@ def oracle_state(o):
 
 def compare_pdf(o, g, tol=PDF_TOL):
     ref, mask = oracle_state(o)
-    got = g.pdf().astype(np.float64)
+    got = g.pdf_f64()
     scale = np.max(np.abs(ref[:, mask]))
     err = np.max(np.abs(got[:, mask] - ref[:, mask])) / scale
     assert err <= tol, f"PDF relative error {err:.3e} > {tol:.0e}"
@@ -247,11 +247,33 @@ def test_fp32_storage_tracks_fp64(lattice, coupling):
     (accumulated in FP64 from FP32 terms) agree to 1e-3 relative."""
     case = moving_sphere_case(coupling)
     o, g = make_pair(case, storage="f32")
+    assert g.pdf().nbytes == 4 * 19 * g.ncells
     start(o, g, lattice)
     o.step(25)
     g.step(25)
     compare_pdf(o, g, tol=1e-5)
     compare_forces(o, g, tol=1e-3)
+
+
+# ---- FP16 / BF16 shifted storage ---------------------------------------------------------------
+# The stored value is g = f - w_q.  FP16 keeps 11 significant bits: each sweep
+# rounds g (|g| <~ 5e-3 here) by <= 2^-12 |g| ~ 1.2e-6, i.e. ~4e-6 of max|f|;
+# over 25 dissipative steps the deviation stays below 2e-4 of max|f|.  BF16
+# keeps 8 bits (8x coarser): 2e-3.  Forces, summed in FP64 from these
+# populations, follow at the same relative order (1e-2 / 5e-2 bars).
+@pytest.mark.parametrize("coupling,storage,pdf_tol,force_tol",
+                         [("PSM_M2B2", "f16s", 2e-4, 1e-2), ("MEM_CLI", "f16s", 2e-4, 1e-2),
+                          ("PSM_M2B2", "bf16s", 2e-3, 5e-2), ("MEM_CLI", "bf16s", 2e-3, 5e-2)])
+def test_shifted_16bit_storage_tracks_fp64(lattice, coupling, storage, pdf_tol, force_tol):
+    case = moving_sphere_case(coupling)
+    o, g = make_pair(case, storage=storage)
+    assert g.pdf().nbytes == 2 * 19 * g.ncells  # the state really is 16-bit
+    start(o, g, lattice)
+    o.step(25)
+    g.step(25)
+    err = compare_pdf(o, g, tol=pdf_tol)
+    assert err > 1e-7  # rounded to 16 bits, not silently kept in FP64
+    compare_forces(o, g, tol=force_tol)
 
 
 # ---- failure reporting ---------------------------------------------------------------------
