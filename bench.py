@@ -154,6 +154,63 @@ def near_cells(particle, shape, halo=2.0):
     return int(count)
 
 
+def run_ensemble(args, stream, world, dist, barrier, peak, storages=("f64", "f64fx")):
+    """The batched ensemble: 64 independent settling cases of uneven size and
+    Galileo number advanced by one captured step graph per global step."""
+    import numpy as np
+    import torch
+
+    from paper_1702_04910_gb300 import workloads as W
+    from paper_1702_04910_gb300.binding import Batch
+
+    cases = W.ensemble(args.ensemble_cases, seed=0)
+    cells = sum(int(np.prod(c["shape"])) for c in cases)
+    near = sum(near_cells(c["particles"][0], c["shape"]) for c in cases)
+    out = {}
+    for storage in storages:
+        b = Batch(cases, storage=storage, stream=stream)
+        layouts, grid, tune_ms = b.autotune(reps=3)
+        b.step(args.warmup)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        b.step(args.steps)
+        ev1.record()
+        barrier()
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+        b.synchronize()  # raises if a case reported a device status
+        parts = b.particles()
+        cu = b.cell_updates
+        bulk_gbps = 2 * 19 * 8 * (cells - near) / (tune_ms * 1e-3) / 1e9
+        out[f"ensemble{len(cases)}_{storage}"] = {
+            "value": world * cu * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ms / args.steps, "steps": args.steps, "cases": len(cases),
+            "cells": cells, "cell_updates_per_step": cu,
+            "workload": "seeded ensemble: D ~ U{8..20}, domain round(5.3D)^2 x round(16D), "
+                        "Ga ~ U(100, 250), density ratio 1.5, PSM M1B1/M2B2 and MEM BB/CLI",
+            "tuning": {"layouts": {k: layouts.count(k) for k in sorted(set(layouts))},
+                       "grid_blocks": grid, "bulk_ms": tune_ms},
+            "bulk_GBps": bulk_gbps, "frac": bulk_gbps / peak,
+            "graph_kernels_per_step": b.graph_kernels,
+            "gpu_launches": b.graph_kernels * args.steps,
+            "device_bytes": b.device_bytes,
+            "mean_particle_uz": float(np.mean([p["u"][2] for p in parts])),
+            "all_particle_states_finite": bool(all(np.all(np.isfinite(p["u"])) for p in parts)),
+        }
+        b.close()
+    return out
+
+
+def run_ensemble_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    peak, _ = measured_peaks()
+    res = run_ensemble(args, stream, 1, None, torch.cuda.synchronize, peak,
+                       storages=tuple(args.ensemble_storage.split(",")))
+    print(json.dumps(res), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -321,6 +378,9 @@ def run_ours(args):
         for s in s64 + sl:
             s.close()
 
+    if not args.no_ensemble:
+        variants.update(run_ensemble(args, stream, world, dist, barrier, peak))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_steps, args.scale)
@@ -472,6 +532,11 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-cases", type=int, default=64)
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="time only the batched ensemble (one JSON object of variants)")
+    ap.add_argument("--ensemble-storage", default="f64,f64fx")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the settling workload by this factor in every length (tests)")
     ap.add_argument("--case-shape", default=None,
@@ -484,6 +549,8 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.case_shape:
         run_case(args)
+    elif args.ensemble_only and args.impl == "ours":
+        run_ensemble_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -49,7 +49,8 @@ typedef enum {
     LBM_ERR_ARG = -1,         /* invalid argument; nothing was changed            */
     LBM_ERR_CUDA = -2,        /* a CUDA runtime call failed                       */
     LBM_ERR_OOM = -3,         /* device or pinned host allocation failed          */
-    LBM_ERR_UNSTABLE = -4,    /* reserved: non-finite state detected              */
+    LBM_ERR_UNSTABLE = -4,    /* a particle state became non-finite or moved a    */
+                              /* cell or more per step (update not applied)       */
     LBM_ERR_DOMAIN = -5,      /* a particle left the domain through a closed wall */
     LBM_ERR_TIMEOUT = -6,     /* reserved: a bounded device wait gave up          */
     LBM_ERR_UNSUPPORTED = -7  /* configuration not implemented (e.g. MEM MR)      */
@@ -265,8 +266,8 @@ lbm_status lbm_sweep_noalloc(const lbm_config *cfg, const double *src_pdf_dev,
  *     tiles of all cases; the near-particle sweep runs beside it;
  *   - the launches of one global step are captured once into a CUDA graph
  *     and replayed by lbm_batch_step;
- *   - lbm_batch_autotune times the bulk sweep for each tile layout and grid
- *     size and keeps the fastest (results do not depend on the choice).
+ *   - lbm_batch_autotune picks each case's tile layout and the bulk grid by
+ *     timing them (results do not depend on the choice).
  * Each case follows the step contract of lbm_step (MEM: lbm_subcycles
  * sweeps, averaged forces, rigid-body update with dt = subcycles, refilling;
  * PSM: one sweep, dt = 1).  The stored state of every case starts as the
@@ -299,17 +300,21 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config *cfgs, const lbm_parti
 /* Enqueues nsteps global steps of every case (graph replays; asynchronous). */
 lbm_status lbm_batch_step(lbm_batch *b, int nsteps);
 
-/* Times the bulk sweep of every layout (LBM_BATCH_*) and grid size (one block
- * per tile, or 1x, 2x, 4x the resident blocks of the GPU) with `reps`
- * launches each (1..100), keeps the fastest and rebuilds the step graph.  The
- * timed launches write only the buffer the next sweep overwrites, so the
- * simulation state is unchanged.  Outputs (each may be NULL): the chosen
- * layout, grid (0 = one block per tile) and its mean launch time in ms. */
-lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *layout, int *grid, double *ms);
+/* Autotuner.  (1) For every case, times the bulk sweep of that case alone in
+ * each tile layout (LBM_BATCH_*) and keeps the fastest, so every case gets
+ * its own block shape; (2) times the bulk sweep of all cases with one block
+ * per tile and with persistent grids of 1x, 2x and 4x the GPU's resident
+ * blocks, keeps the fastest, and rebuilds the step graph.  `reps` (1..100)
+ * launches per measurement.  The timed launches write only the buffer the
+ * next sweep overwrites, so the simulation state is unchanged (results do
+ * not depend on the tuning).  Outputs, each may be NULL: layouts[n_cases],
+ * the grid (0 = one block per tile) and the mean bulk-sweep time in ms. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *layouts, int *grid, double *ms);
 
-/* Sets the bulk layout (LBM_BATCH_*) and grid (0 = one block per tile, else
- * the number of persistent blocks) explicitly and rebuilds the step graph. */
-lbm_status lbm_batch_set_tuning(lbm_batch *b, int layout, int grid);
+/* Sets the bulk layout of every case (layouts[n_cases], LBM_BATCH_*; NULL:
+ * all LBM_BATCH_PLANE) and the grid (0 = one block per tile, else the number
+ * of persistent blocks), then rebuilds the step graph. */
+lbm_status lbm_batch_set_tuning(lbm_batch *b, const int *layouts, int grid);
 
 /* Particle state of every case (n_cases records; synchronises). */
 lbm_status lbm_batch_get_particles(lbm_batch *b, lbm_particle *host_out);

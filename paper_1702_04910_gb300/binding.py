@@ -36,7 +36,12 @@ PROFILE_CLASSES = ("bulk", "near", "force_total", "rigid_body", "refill", "other
 EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_equilibrium",
             "lbm_step", "lbm_get_forces", "lbm_get_fields", "lbm_set_fields",
             "lbm_synchronize", "lbm_profile_enable", "lbm_profile_read", "lbm_device_bytes",
-            "lbm_destroy", "lbm_last_error", "lbm_abi_version", "lbm_sweep_noalloc")
+            "lbm_destroy", "lbm_last_error", "lbm_abi_version", "lbm_sweep_noalloc",
+            "lbm_batch_create", "lbm_batch_step", "lbm_batch_autotune", "lbm_batch_set_tuning",
+            "lbm_batch_get_particles", "lbm_batch_get_forces", "lbm_batch_get_pdf",
+            "lbm_batch_cell_updates", "lbm_batch_device_bytes", "lbm_batch_graph_kernels",
+            "lbm_batch_synchronize", "lbm_batch_destroy", "lbm_batch_last_error")
+BATCH_LAYOUTS = {"box32": 0, "box64": 1, "box128": 2, "plane": 3}
 
 
 class LbmConfig(ct.Structure):
@@ -97,6 +102,20 @@ def load(build_if_missing: bool = True):
             "lbm_abi_version": (i, []),
             "lbm_sweep_noalloc": (i, [ct.POINTER(LbmConfig), vp, vp, i, ct.POINTER(LbmParticle),
                                       vp, vp, vp, ct.c_char_p, sz]),
+            "lbm_batch_create": (i, [i, ct.POINTER(LbmConfig), ct.POINTER(LbmParticle), vp,
+                                     ct.POINTER(vp)]),
+            "lbm_batch_step": (i, [vp, i]),
+            "lbm_batch_autotune": (i, [vp, i, ct.POINTER(i), ct.POINTER(i), dp]),
+            "lbm_batch_set_tuning": (i, [vp, ct.POINTER(i), i]),
+            "lbm_batch_get_particles": (i, [vp, ct.POINTER(LbmParticle)]),
+            "lbm_batch_get_forces": (i, [vp, dp, dp]),
+            "lbm_batch_get_pdf": (i, [vp, i, dp, sz]),
+            "lbm_batch_cell_updates": (ct.c_longlong, [vp]),
+            "lbm_batch_device_bytes": (sz, [vp]),
+            "lbm_batch_graph_kernels": (i, [vp]),
+            "lbm_batch_synchronize": (i, [vp]),
+            "lbm_batch_destroy": (None, [vp]),
+            "lbm_batch_last_error": (ct.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -228,6 +247,86 @@ def lbm_device_bytes(h) -> int:
     return int(load().lbm_device_bytes(h))
 
 
+# ---- batched ensemble (C names) ------------------------------------------------------
+def _bcheck(b, st):
+    if st != LBM_OK:
+        msg = load().lbm_batch_last_error(b)
+        raise LbmError(st, msg.decode() if msg else "")
+    return st
+
+
+def lbm_batch_create(cfgs, particles, stream: int | None = None) -> ct.c_void_p:
+    """cfgs: list of LbmConfig; particles: one particle dict per case."""
+    n = len(cfgs)
+    carr = (LbmConfig * n)(*cfgs)
+    parr = particles_to_c(particles)
+    b = ct.c_void_p()
+    _bcheck(None, load().lbm_batch_create(n, carr, parr, ct.c_void_p(stream or 0), ct.byref(b)))
+    return b
+
+
+def lbm_batch_step(b, nsteps: int) -> None:
+    _bcheck(b, load().lbm_batch_step(b, int(nsteps)))
+
+
+def lbm_batch_autotune(b, n: int, reps: int = 5):
+    """Returns (per-case layouts, grid, bulk ms)."""
+    lays = (ct.c_int * n)()
+    grid, ms = ct.c_int(), ct.c_double()
+    _bcheck(b, load().lbm_batch_autotune(b, int(reps), lays, ct.byref(grid), ct.byref(ms)))
+    return list(lays), grid.value, ms.value
+
+
+def lbm_batch_set_tuning(b, layouts, grid: int) -> None:
+    """layouts: one LBM_BATCH_* code per case, or None (all plane)."""
+    arr = None if layouts is None else (ct.c_int * len(layouts))(*[int(v) for v in layouts])
+    _bcheck(b, load().lbm_batch_set_tuning(b, arr, int(grid)))
+
+
+def lbm_batch_get_particles(b, n: int):
+    arr = (LbmParticle * n)()
+    _bcheck(b, load().lbm_batch_get_particles(b, arr))
+    return [{"x": np.array(arr[i].x[:]), "u": np.array(arr[i].u[:]),
+             "omega": np.array(arr[i].omega[:]), "diameter": arr[i].diameter,
+             "density": arr[i].density, "fixed": arr[i].fixed} for i in range(n)]
+
+
+def lbm_batch_get_forces(b, n: int):
+    F = np.zeros((n, 3))
+    T = np.zeros((n, 3))
+    _bcheck(b, load().lbm_batch_get_forces(b, F.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                           T.ctypes.data_as(ct.POINTER(ct.c_double))))
+    return F, T
+
+
+def lbm_batch_get_pdf(b, c: int, shape) -> np.ndarray:
+    nx, ny, nz = shape
+    out = np.empty((NQ, nz, ny, nx))
+    _bcheck(b, load().lbm_batch_get_pdf(b, int(c), out.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                        out.nbytes))
+    return out
+
+
+def lbm_batch_cell_updates(b) -> int:
+    return int(load().lbm_batch_cell_updates(b))
+
+
+def lbm_batch_device_bytes(b) -> int:
+    return int(load().lbm_batch_device_bytes(b))
+
+
+def lbm_batch_graph_kernels(b) -> int:
+    return int(load().lbm_batch_graph_kernels(b))
+
+
+def lbm_batch_synchronize(b) -> None:
+    _bcheck(b, load().lbm_batch_synchronize(b))
+
+
+def lbm_batch_destroy(b) -> None:
+    load().lbm_batch_destroy(b)
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 class Simulation:
     """One library handle; arrays are NumPy (host) unless noted."""
@@ -321,3 +420,67 @@ class Simulation:
 
     def synchronize(self):
         lbm_synchronize(self.h)
+
+
+class Batch:
+    """A batched ensemble: ``cases`` are workload dicts with one particle each
+    (shape, solver keywords, particles)."""
+
+    def __init__(self, cases, storage: str = "f64", stream: int | None = None):
+        from .workloads import sim_kwargs
+        self.shapes = [tuple(int(v) for v in c["shape"]) for c in cases]
+        cfgs = [make_config(c["shape"], storage=storage, **sim_kwargs(c)) for c in cases]
+        self.n = len(cases)
+        self.b = lbm_batch_create(cfgs, [c["particles"][0] for c in cases], stream)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    def autotune(self, reps=5):
+        """Per-case layouts (names), grid, bulk ms."""
+        lays, grid, ms = lbm_batch_autotune(self.b, self.n, reps)
+        names = {v: k for k, v in BATCH_LAYOUTS.items()}
+        return [names[v] for v in lays], grid, ms
+
+    def set_tuning(self, layout, grid):
+        """layout: a name or code for every case, or a list with one per case."""
+        if isinstance(layout, (list, tuple)):
+            lays = [BATCH_LAYOUTS.get(v, v) for v in layout]
+        else:
+            lays = [BATCH_LAYOUTS.get(layout, layout)] * self.n
+        lbm_batch_set_tuning(self.b, lays, grid)
+
+    def particles(self):
+        return lbm_batch_get_particles(self.b, self.n)
+
+    def forces(self):
+        return lbm_batch_get_forces(self.b, self.n)
+
+    def pdf(self, c):
+        return lbm_batch_get_pdf(self.b, c, self.shapes[c])
+
+    @property
+    def cell_updates(self):
+        return lbm_batch_cell_updates(self.b)
+
+    @property
+    def device_bytes(self):
+        return lbm_batch_device_bytes(self.b)
+
+    @property
+    def graph_kernels(self):
+        return lbm_batch_graph_kernels(self.b)
+
+    def synchronize(self):
+        lbm_batch_synchronize(self.b)

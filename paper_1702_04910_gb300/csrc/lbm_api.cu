@@ -301,6 +301,9 @@ lbm_status read_status(lbm_handle* h) {
     if (st) {
         CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream), "status reset");
         if (st & ST_DOMAIN) return fail(h, LBM_ERR_DOMAIN, "a particle left the domain through a closed wall");
+        if (st & ST_UNSTABLE)
+            return fail(h, LBM_ERR_UNSTABLE,
+                        "a particle state became non-finite or moved a cell or more per step");
         if (st & ST_TOO_MANY_OBJECTS)
             return fail(h, LBM_ERR_UNSUPPORTED, "more than two particles touch one cell");
         return fail(h, LBM_ERR_CUDA, "device status raised");

@@ -70,7 +70,8 @@ struct lbm_batch {
     double* dforce;
     WorkList map_l, refill_l;
     std::vector<WorkList> near_l, bulk_l;  // per subcycle
-    int layout;
+    WorkList one;              // single-case list used by the autotuner
+    std::vector<int> layouts;  // bulk tiling of each case (LBM_BATCH_*)
     int grid;
     int resident;  // resident bulk blocks on the GPU (SMs x blocks per SM)
     cudaGraph_t graph;
@@ -145,26 +146,32 @@ lbm_status upload_list(lbm_batch* b, WorkList& w) {
     return LBM_OK;
 }
 
-// Applies a bulk layout: re-tiles every case, recomputes the particle
-// regions' tile ranges and the bulk work lists.  The caller synchronises.
-lbm_status apply_layout(lbm_batch* b, int layout) {
-    for (auto& c : b->hc) set_tiling(c.g, layout);
-    // cur lives on the device and is flipped there: write only the geometry
-    for (int i = 0; i < b->n; ++i)
-        BK(b, cudaMemcpyAsync(&b->dcases[i].g, &b->hc[i].g, sizeof(Geom), cudaMemcpyHostToDevice,
+// Applies per-case bulk layouts: re-tiles every case, recomputes the
+// particle regions' tile ranges and the bulk work lists.  Synchronises.
+lbm_status apply_layouts(lbm_batch* b, const std::vector<int>& lays) {
+    for (int i = 0; i < b->n; ++i) {
+        BatchCase& c = b->hc[i];
+        set_tiling(c.g, lays[i]);
+        c.layout = lays[i] == LBM_BATCH_PLANE ? 1 : 0;
+        // cur lives on the device and is flipped there: write only the tiling
+        BK(b, cudaMemcpyAsync(&b->dcases[i].g, &c.g, sizeof(Geom), cudaMemcpyHostToDevice,
                               b->stream),
            "case upload");
+        BK(b, cudaMemcpyAsync(&b->dcases[i].layout, &c.layout, sizeof(int), cudaMemcpyHostToDevice,
+                              b->stream),
+           "case upload");
+    }
     BK(b, launch_batch_regions(b->dcases, b->n, b->stream), "region launch");
     for (int s = 0; s < b->max_sub; ++s) {
         std::vector<long long> items;
-        for (int c : b->bulk_l[s].h_list) items.push_back(bulk_items(b->hc[c].g, layout));
+        for (int c : b->bulk_l[s].h_list) items.push_back(bulk_items(b->hc[c].g, lays[c]));
         std::vector<int> cases = b->bulk_l[s].h_list;
         fill_list(b->bulk_l[s], cases, items);
         lbm_status st = upload_list(b, b->bulk_l[s]);
         if (st != LBM_OK) return st;
     }
     BK(b, cudaStreamSynchronize(b->stream), "layout sync");  // host vectors above are pageable
-    b->layout = layout;
+    b->layouts = lays;
     return LBM_OK;
 }
 
@@ -190,8 +197,7 @@ cudaError_t enqueue_step(lbm_batch* b, int* kernels) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
         if (e == cudaSuccess) e = launch_batch_near(b->dcases, nl.view(), nl.total, sub, b->dstatus, b->side);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
-        if (e == cudaSuccess) e = launch_batch_bulk(b->mode, b->layout == LBM_BATCH_PLANE ? 1 : 0,
-                                                    b->dcases, bl.view(), bl.total, b->grid, s);
+        if (e == cudaSuccess) e = launch_batch_bulk(b->mode, b->dcases, bl.view(), bl.total, b->grid, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
         if (e == cudaSuccess) e = launch_batch_swap(b->dcases, nl.view(), s);
         k += 3;
@@ -234,6 +240,9 @@ lbm_status read_status(lbm_batch* b) {
     if (st) {
         BK(b, cudaMemsetAsync(b->dstatus, 0, sizeof(int), b->stream), "status reset");
         if (st & ST_DOMAIN) return fail(b, LBM_ERR_DOMAIN, "a particle left the domain through a closed wall");
+        if (st & ST_UNSTABLE)
+            return fail(b, LBM_ERR_UNSTABLE,
+                        "a particle state became non-finite or moved a cell or more per step");
         if (st & ST_TOO_MANY_OBJECTS) return fail(b, LBM_ERR_UNSUPPORTED, "more than two particles touch one cell");
         return fail(b, LBM_ERR_CUDA, "device status raised");
     }
@@ -346,16 +355,14 @@ void release(lbm_batch* b) {
     delete b;
 }
 
-// Mean duration (ms) of `reps` launches of the first sweep's bulk kernel at
-// the current layout and the given grid.  src = buf[cur], dst = buf[1 - cur]:
-// the next sweep overwrites every cell this writes.
-lbm_status time_bulk(lbm_batch* b, int grid, int reps, double* ms) {
-    const WorkList& bl = b->bulk_l[0];
-    const int lay = b->layout == LBM_BATCH_PLANE ? 1 : 0;
-    BK(b, launch_batch_bulk(b->mode, lay, b->dcases, bl.view(), bl.total, grid, b->stream), "tuning launch");
+// Mean duration (ms) of `reps` launches of the bulk kernel over list w at
+// the given grid.  src = buf[cur], dst = buf[1 - cur]: the next sweep
+// overwrites every cell this writes, so the simulation state is unchanged.
+lbm_status time_bulk(lbm_batch* b, const WorkList& w, int grid, int reps, double* ms) {
+    BK(b, launch_batch_bulk(b->mode, b->dcases, w.view(), w.total, grid, b->stream), "tuning launch");
     BK(b, cudaEventRecord(b->t0, b->stream), "event record");
     for (int r = 0; r < reps; ++r)
-        BK(b, launch_batch_bulk(b->mode, lay, b->dcases, bl.view(), bl.total, grid, b->stream),
+        BK(b, launch_batch_bulk(b->mode, b->dcases, w.view(), w.total, grid, b->stream),
            "tuning launch");
     BK(b, cudaEventRecord(b->t1, b->stream), "event record");
     BK(b, cudaEventSynchronize(b->t1), "event sync");
@@ -454,7 +461,9 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
         ol = take(sizeof(int) * std::max(w.n, 1));
         ob = take(sizeof(long long) * (w.n + 1));
     };
-    size_t ml, mb, rl, rb;
+    size_t ml, mb, rl, rb, ol, ob;
+    b->one.n = 1;
+    list_off(b->one, ol, ob);
     list_off(b->map_l, ml, mb);
     list_off(b->refill_l, rl, rb);
     std::vector<size_t> nl(b->max_sub), nb(b->max_sub), bl(b->max_sub), bb(b->max_sub);
@@ -497,6 +506,7 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
         w.list = (int*)(base + ol);
         w.base = (long long*)(base + ob);
     };
+    bind(b->one, ol, ob);
     bind(b->map_l, ml, mb);
     bind(b->refill_l, rl, rb);
     for (int s = 0; s < b->max_sub; ++s) {
@@ -527,7 +537,7 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
     for (auto& k : b->hc) max_cells = std::max(max_cells, k.g.n);
     if (st == LBM_OK && (e = launch_batch_init(b->dcases, n_cases, max_cells, b->stream)) != cudaSuccess)
         st = cuda_fail(b, e, "init launch");
-    if (st == LBM_OK) st = apply_layout(b, LBM_BATCH_PLANE);  // synchronises
+    if (st == LBM_OK) st = apply_layouts(b, std::vector<int>(n_cases, LBM_BATCH_PLANE));
     if (st == LBM_OK) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -551,42 +561,60 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     return LBM_OK;
 }
 
-lbm_status lbm_batch_set_tuning(lbm_batch* b, int layout, int grid) {
-    if (!b || layout < LBM_BATCH_BOX32 || layout > LBM_BATCH_PLANE || grid < 0 || grid > (1 << 24))
-        return fail(b, LBM_ERR_ARG, "layout must be 0..3 and grid >= 0");
+lbm_status lbm_batch_set_tuning(lbm_batch* b, const int* layouts, int grid) {
+    if (!b) return LBM_ERR_ARG;
+    if (grid < 0 || grid > (1 << 24)) return fail(b, LBM_ERR_ARG, "grid must be 0..2^24");
+    std::vector<int> lays(b->n, LBM_BATCH_PLANE);
+    for (int i = 0; layouts && i < b->n; ++i) {
+        if (layouts[i] < LBM_BATCH_BOX32 || layouts[i] > LBM_BATCH_PLANE)
+            return fail(b, LBM_ERR_ARG, "layouts must be LBM_BATCH_BOX32..LBM_BATCH_PLANE");
+        lays[i] = layouts[i];
+    }
     BK(b, cudaStreamSynchronize(b->stream), "tuning sync");
-    lbm_status st = layout != b->layout ? apply_layout(b, layout) : LBM_OK;
+    lbm_status st = apply_layouts(b, lays);
     if (st != LBM_OK) return st;
     b->grid = grid;
     return build_graph(b);
 }
 
-lbm_status lbm_batch_autotune(lbm_batch* b, int reps, int* layout, int* grid, double* ms) {
+lbm_status lbm_batch_autotune(lbm_batch* b, int reps, int* layouts, int* grid, double* ms) {
     if (!b || reps < 1 || reps > 100) return fail(b, LBM_ERR_ARG, "reps must be 1..100");
     BK(b, cudaStreamSynchronize(b->stream), "tuning sync");
-    const int grids[4] = {0, b->resident, 2 * b->resident, 4 * b->resident};
-    double best = 1e300;
-    int best_l = b->layout, best_g = b->grid;
+    // 1. per case: the layout whose bulk sweep of that case alone is fastest
+    std::vector<double> best_t(b->n, 1e300);
+    std::vector<int> best_l(b->n, LBM_BATCH_PLANE);
     for (int lay = LBM_BATCH_BOX32; lay <= LBM_BATCH_PLANE; ++lay) {
-        lbm_status st = apply_layout(b, lay);
+        lbm_status st = apply_layouts(b, std::vector<int>(b->n, lay));
         if (st != LBM_OK) return st;
-        for (int gi = 0; gi < 4; ++gi) {
+        for (int c = 0; c < b->n; ++c) {
+            fill_list(b->one, std::vector<int>{c}, std::vector<long long>{bulk_items(b->hc[c].g, lay)});
+            if ((st = upload_list(b, b->one)) != LBM_OK) return st;
             double t = 0.0;
-            st = time_bulk(b, grids[gi], reps, &t);
-            if (st != LBM_OK) return st;
-            if (t < best) {
-                best = t;
-                best_l = lay;
-                best_g = grids[gi];
+            if ((st = time_bulk(b, b->one, 0, reps, &t)) != LBM_OK) return st;  // synchronises
+            if (t < best_t[c]) {
+                best_t[c] = t;
+                best_l[c] = lay;
             }
         }
     }
-    lbm_status st = apply_layout(b, best_l);
+    lbm_status st = apply_layouts(b, best_l);
     if (st != LBM_OK) return st;
+    // 2. for the whole first sweep: one block per tile or a persistent grid
+    const int grids[4] = {0, b->resident, 2 * b->resident, 4 * b->resident};
+    double best = 1e300;
+    int best_g = 0;
+    for (int gi = 0; gi < 4; ++gi) {
+        double t = 0.0;
+        if ((st = time_bulk(b, b->bulk_l[0], grids[gi], reps, &t)) != LBM_OK) return st;
+        if (t < best) {
+            best = t;
+            best_g = grids[gi];
+        }
+    }
     b->grid = best_g;
-    st = build_graph(b);
-    if (st != LBM_OK) return st;
-    if (layout) *layout = best_l;
+    if ((st = build_graph(b)) != LBM_OK) return st;
+    if (layouts)
+        for (int c = 0; c < b->n; ++c) layouts[c] = best_l[c];
     if (grid) *grid = best_g;
     if (ms) *ms = best;
     return LBM_OK;

@@ -503,6 +503,16 @@ __device__ __forceinline__ void rigid_one(const Geom& g, DevParticle* __restrict
         for (int a = 0; a < 3; ++a) P.x[a] += dt * P.u[a];
         for (int a = 0; a < 3; ++a) P.u[a] += dt * Ft[a] / m;
         for (int a = 0; a < 3; ++a) P.w[a] += dt * force[3 + a] / I;
+        // a non-finite state, or a surface moving a cell or more per step,
+        // is outside what the lattice can represent: report it and keep the
+        // previous state so that the cell geometry stays well defined
+        bool sane = true;
+        for (int a = 0; a < 3; ++a)
+            sane = sane && isfinite(P.x[a]) && fabs(P.u[a]) < 1.0 && fabs(P.w[a]) * R < 1.0;
+        if (!sane) {
+            atomicOr(status, ST_UNSTABLE);
+            P = *prev;
+        }
         const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
         for (int a = 0; a < 3; ++a) {
             if (a == 2 && g.bc_z) continue;
@@ -934,9 +944,10 @@ __device__ __forceinline__ void bulk_segment(const double* __restrict__ src,
 }
 
 // bulk sweep: persistent 256-thread blocks striding over the tiles of all
-// listed cases.  LAYOUT 0: box tiles of the case's g.tx x g.ty cells (thread
-// t -> (t mod g.tx, t / g.tx)); LAYOUT 1: 256-cell plane segments.
-template <typename C, int LAYOUT>
+// listed cases.  Each case has its own tiling (B.layout, chosen by the
+// autotuner): 0 box tiles of g.tx x g.ty cells (thread t -> (t mod g.tx,
+// t / g.tx)); 1 plane segments of 256 cells.
+template <typename C>
 __global__ void __launch_bounds__(256, BulkBlocks<C>::value)
     k_batch_bulk(BatchCase* __restrict__ cases, BatchList l, long long total) {
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -944,7 +955,7 @@ __global__ void __launch_bounds__(256, BulkBlocks<C>::value)
         const BatchCase& B = cases[l.list[i]];
         const long long local = t - l.base[i];
         const int cur = B.cur;
-        if (LAYOUT == 1) {
+        if (B.layout == 1) {
             const int nseg = (B.g.nx * B.g.ny + 255) / 256;
             bulk_segment<C>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B), B.part->reg,
                             (int)(local % nseg), (int)(local / nseg), threadIdx.x);
@@ -1237,17 +1248,14 @@ cudaError_t launch_batch_near(BatchCase* cases, BatchList l, long long total, in
     k_batch_near<<<(unsigned)total, dim3(NEAR_BX, NEAR_BY, NEAR_BZ), 0, s>>>(cases, l, sub, status);
     return cudaGetLastError();
 }
-cudaError_t launch_batch_bulk(int mode, int layout, BatchCase* cases, BatchList l,
-                              long long total, int grid, cudaStream_t s) {
+cudaError_t launch_batch_bulk(int mode, BatchCase* cases, BatchList l, long long total, int grid,
+                              cudaStream_t s) {
     if (l.n == 0 || total == 0) return cudaSuccess;
     const unsigned gsz = (unsigned)(grid <= 0 || total < grid ? total : grid);
-    if (mode == 3) {
-        if (layout == 1) k_batch_bulk<fx64, 1><<<gsz, 256, 0, s>>>(cases, l, total);
-        else k_batch_bulk<fx64, 0><<<gsz, 256, 0, s>>>(cases, l, total);
-    } else {
-        if (layout == 1) k_batch_bulk<double, 1><<<gsz, 256, 0, s>>>(cases, l, total);
-        else k_batch_bulk<double, 0><<<gsz, 256, 0, s>>>(cases, l, total);
-    }
+    if (mode == 3)
+        k_batch_bulk<fx64><<<gsz, 256, 0, s>>>(cases, l, total);
+    else
+        k_batch_bulk<double><<<gsz, 256, 0, s>>>(cases, l, total);
     return cudaGetLastError();
 }
 cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s) {
@@ -1272,9 +1280,9 @@ cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, 
 int batch_bulk_blocks_per_sm(int mode) {
     int nb = 0;
     if (mode == 3)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<fx64, 0>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<fx64>, 256, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<double, 0>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<double>, 256, 0);
     return nb > 0 ? nb : 1;
 }
 

@@ -75,6 +75,7 @@ struct BatchCase {
     int cur;
     int kind;          // 1 PSM, 2 MEM, 0 none
     int subcycles;     // LBM sweeps per global step
+    int layout;        // bulk tiling: 0 box tiles (g.tx x g.ty), 1 256-cell plane segments
     int wall_contact;
     Coupl cp;          // np = 1
     Coll<double> kd;
@@ -136,6 +137,7 @@ enum : int {
     ST_TOO_MANY_OBJECTS = 1,  // more than CELL_SLOTS particles touch a cell
     ST_DOMAIN = 2,            // a particle left the domain through a closed wall
     ST_REFILL_SOLID = 4,      // refill found no particle owning a cell (internal)
+    ST_UNSTABLE = 8,          // a particle state became non-finite or too fast
 };
 
 // storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision), 4 = FP16
@@ -160,10 +162,9 @@ cudaError_t launch_batch_regions(BatchCase* cases, int n, cudaStream_t s);
 cudaError_t launch_batch_map(BatchCase* cases, BatchList l, long long total, cudaStream_t s);
 cudaError_t launch_batch_near(BatchCase* cases, BatchList l, long long total, int sub,
                               int* status, cudaStream_t s);
-// mode 0 FP64 / 3 fixed-point collision; layout 0 box tiles (case's g.tx),
-// 1 plane segments; grid <= 0: one block per tile
-cudaError_t launch_batch_bulk(int mode, int layout, BatchCase* cases, BatchList l,
-                              long long total, int grid, cudaStream_t s);
+// mode 0 FP64 / 3 fixed-point collision; grid <= 0: one block per tile
+cudaError_t launch_batch_bulk(int mode, BatchCase* cases, BatchList l, long long total, int grid,
+                              cudaStream_t s);
 cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s);
 cudaError_t launch_batch_finalize(BatchCase* cases, int n, cudaStream_t s);
 cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_t s);

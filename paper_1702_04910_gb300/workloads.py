@@ -93,3 +93,39 @@ def sim_kwargs(case: dict) -> dict:
     keys = ("coupling", "collision", "tau", "magic", "fext", "gravity", "rho0", "bc_z",
             "subsample", "subcycles", "wall_contact")
     return {k: case[k] for k in keys}
+
+
+ENSEMBLE_COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI")
+
+
+def ensemble(n_cases: int = 64, seed: int = 0, d_range=(8, 20), ga_range=(100.0, 250.0),
+             density_ratio: float = 1.5, couplings=ENSEMBLE_COUPLINGS, u_ref: float = 0.05,
+             nu_min: float = 0.002, collision: str = "TRT") -> list[dict]:
+    """Independent settling-sphere cases of uneven size and Galileo number.
+
+    Case c: D drawn uniformly from the integers d_range (inclusive), domain
+    round(5.3 D) x round(5.3 D) x round(16 D) cells (closed top and bottom,
+    periodic sides), Galileo number uniform in ga_range, the coupling
+    couplings[c mod len], and the viscosity that gives a reference velocity
+    Ga nu / D of ``u_ref`` (bounded below by ``nu_min``, i.e. tau >= 0.506).
+    The sphere starts at rest 8/3 D below the top (the 64-cells-at-D=24
+    release height of the single settling workload) with a seeded lateral
+    offset of up to a quarter cell.
+    """
+    rng = np.random.default_rng(seed)
+    cases = []
+    for c in range(n_cases):
+        D = float(rng.integers(d_range[0], d_range[1] + 1))
+        ga = float(rng.uniform(*ga_range))
+        nu = max(u_ref * D / ga, nu_min)
+        shape = (int(round(5.3 * D)), int(round(5.3 * D)), int(round(16.0 * D)))
+        off = rng.uniform(-0.25, 0.25, size=2)
+        case = settling_sphere(D=D, shape=shape, ga=ga, nu=nu, density_ratio=density_ratio,
+                               drop_below_top=8.0 * D / 3.0,
+                               coupling=couplings[c % len(couplings)], collision=collision)
+        x = list(case["particles"][0]["x"])
+        x[0] += off[0]
+        x[1] += off[1]
+        case["particles"][0]["x"] = tuple(x)
+        cases.append(case)
+    return cases

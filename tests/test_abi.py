@@ -100,5 +100,49 @@ def test_binding_wrapper_surface():
                  "synchronize", "close"):
         assert callable(getattr(binding.Simulation, name)), name
     for name in binding.EXPORTED:
-        if name not in ("lbm_last_error", "lbm_abi_version"):
+        if name not in ("lbm_last_error", "lbm_abi_version", "lbm_batch_last_error"):
             assert callable(getattr(binding, name)), name
+    for name in ("step", "autotune", "set_tuning", "particles", "forces", "pdf", "synchronize",
+                 "close"):
+        assert callable(getattr(binding.Batch, name)), name
+
+
+def test_batch_rejects_invalid_cases_without_gpu():
+    """lbm_batch_create validates every case before any CUDA call and leaves
+    the reason readable through lbm_batch_last_error(NULL)."""
+    from paper_1702_04910_gb300 import workloads as W
+    lib = binding.load()
+    cases = W.ensemble(3, seed=1, d_range=(5, 6))
+
+    def create(cfgs, parts):
+        carr = (binding.LbmConfig * len(cfgs))(*cfgs)
+        b = ct.c_void_p()
+        st = lib.lbm_batch_create(len(cfgs), carr, binding.particles_to_c(parts), None,
+                                  ct.byref(b))
+        return st, lib.lbm_batch_last_error(None).decode()
+
+    def cfgs_of(cs, **over):
+        out = []
+        for c in cs:
+            kw = W.sim_kwargs(c)
+            kw.update(over)
+            out.append(binding.make_config(c["shape"], **kw))
+        return out
+
+    parts = [c["particles"][0] for c in cases]
+    st, msg = create(cfgs_of(cases, coupling="MEM_MR"), parts)
+    assert st == binding.LBM_ERR_UNSUPPORTED and "case 0" in msg
+    st, msg = create(cfgs_of(cases, coupling="NONE"), parts)
+    assert st == binding.LBM_ERR_ARG
+    cfgs = cfgs_of(cases)
+    cfgs[2].storage = binding.STORAGE["f64fx"]
+    st, msg = create(cfgs, parts)
+    assert st == binding.LBM_ERR_ARG and "case 2" in msg and "storage" in msg
+    st, msg = create(cfgs_of(cases, storage="f32"), parts)
+    assert st == binding.LBM_ERR_UNSUPPORTED
+    big = [dict(p) for p in parts]
+    big[1]["diameter"] = 100.0
+    st, msg = create(cfgs_of(cases), big)
+    assert st == binding.LBM_ERR_ARG and "case 1" in msg
+    st, msg = create([], [])
+    assert st == binding.LBM_ERR_ARG
