@@ -32,6 +32,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % of HBM roofline, coupled D3Q19 step; force/velocity error vs FP64"
+# k_bulk with FP64 arithmetic is bound by the FP64 pipe (2 FP64 lane-operations
+# per SM per cycle on GB300, ncu peak_sustained): its roofline counts FP64
+# thread-instructions per cell update, measured by ncu on the 128x128x256
+# settling case (profiles/k_bulk_f64_settling_128x128x256.md), and the DRAM
+# bytes per cell update of the same capture (None once the kernel changes).
+K_BULK_F64_DP_INST_PER_CELL = 124.2
+K_BULK_F64_DRAM_BYTES_PER_CELL = None
+FP64_LANE_OPS_PER_SM_CLK = 2
 COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI")
 SHAPE = (128, 128, 512)
 WORKLOAD = ("settling sphere 128x128x512, D=24, rho_p/rho_f=1.5, Ga=144 (nu=0.01, tau=0.53), "
@@ -199,6 +207,32 @@ def run_ensemble(args, stream, world, dist, barrier, peak, storages=("f64", "f64
         }
         b.close()
     return out
+
+
+def run_learned(args, stream):
+    """Learned force correction: coarse runs corrected towards fine runs of the
+    same method; held-out Galileo numbers scored against the plain FP64 fine
+    run ("small": D 6 vs 24; "full": D 12 on 64x64x192 in FP32 vs D 48 on
+    256x256x768 in FP64)."""
+    from paper_1702_04910_gb300 import learned as LR
+
+    full = args.learned == "full"
+    res = LR.experiment(train_ga=[110.0, 170.0, 240.0], test_ga=[140.0, 210.0],
+                        coupling="PSM_M2B2", D_c=12.0 if full else 6.0, ratio=4,
+                        t_refs=6.0 if full else 5.0, train_steps=3000, stream=stream,
+                        coarse_storage="f32" if full else "f64")
+    res.pop("model").close()
+    held = {g: r for g, r in res["cases"].items() if r["held_out"]}
+    return {
+        "workload": f"settling sphere Ga {res['test_ga']} held out; coarse D={res['D_coarse']:.0f} "
+                    f"({res['coarse_storage']}) corrected towards D={res['D_fine']:.0f} (f64), "
+                    f"{res['coupling']}",
+        "settling_velocity_rel_error_plain": {g: r["plain"]["mean_rel_error"] for g, r in held.items()},
+        "settling_velocity_rel_error_corrected": {g: r["corrected"]["mean_rel_error"] for g, r in held.items()},
+        "speedup_vs_fine_fp64": res["speedup_vs_fine_fp64"],
+        "training_loss": [res["loss_history"][0], res["loss_history"][-1]],
+        "samples": res["samples"], "coarse_steps": res["coarse_steps"],
+    }
 
 
 def run_ensemble_only(args):
@@ -380,6 +414,29 @@ def run_ours(args):
 
     if not args.no_ensemble:
         variants.update(run_ensemble(args, stream, world, dist, barrier, peak))
+    if args.learned != "none" and world == 1:
+        variants[f"learned_{args.learned}"] = run_learned(args, stream)
+
+    # dominant kernel's roofline: the FP64 pipe (HBM fraction kept beside it)
+    props = torch.cuda.get_device_properties(local)
+    sm_max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    fp64_peak = FP64_LANE_OPS_PER_SM_CLK * props.multi_processor_count * sm_max_mhz * 1e6 / 1e12
+    launch_s = bulk_ms / bulk_n * 1e-3
+    fp64_achieved = K_BULK_F64_DP_INST_PER_CELL * bulk_cells / launch_s / 1e12
+    traffic = (None if K_BULK_F64_DRAM_BYTES_PER_CELL is None
+               else K_BULK_F64_DRAM_BYTES_PER_CELL * bulk_cells)
+    roofline = {
+        "bound": "alu", "kernel": "k_bulk (fused pull stream + TRT collide), FP64 pipe",
+        "achieved": fp64_achieved, "peak": fp64_peak, "unit": "T FP64 inst/s",
+        "frac": fp64_achieved / fp64_peak,
+        "peak_source": f"{FP64_LANE_OPS_PER_SM_CLK} FP64 lane-ops/SM/cycle x "
+                       f"{props.multi_processor_count} SMs x {sm_max_mhz:.0f} MHz",
+        "per_unit": f"{K_BULK_F64_DP_INST_PER_CELL} FP64 instructions per cell update (ncu)",
+        "cells_per_launch": bulk_cells, "avg_launch_ms": bulk_ms / bulk_n,
+        "traffic": traffic,
+        "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind, "algorithmic_bytes_per_cell": bytes_per_cell},
+    }
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -397,12 +454,7 @@ def run_ours(args):
                        "precision": "FP64 PDFs and collision; FP64 forces and rigid-body update",
                        "l2": "inputs larger than L2 (2.55 GB of PDFs per simulation)",
                        "replicas_per_rank": 1},
-            "roofline": {"bound": "hbm", "kernel": "k_bulk (fused pull stream + TRT collide)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind,
-                         "algorithmic_bytes_per_cell": bytes_per_cell,
-                         "cells_per_launch": bulk_cells,
-                         "avg_launch_ms": bulk_ms / bulk_n, "traffic": None},
+            "roofline": roofline,
             "kernel_time_share": {k: (v / tot if tot else 0.0) for k, v in share.items()},
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d // args.steps,
                     "d2h_bytes_per_step": d2h // args.steps,
@@ -537,6 +589,9 @@ def main():
     ap.add_argument("--ensemble-only", action="store_true",
                     help="time only the batched ensemble (one JSON object of variants)")
     ap.add_argument("--ensemble-storage", default="f64,f64fx")
+    ap.add_argument("--learned", choices=("small", "full", "none"), default="small",
+                    help="learned force correction study reported as a variant")
+    ap.add_argument("--learned-only", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the settling workload by this factor in every length (tests)")
     ap.add_argument("--case-shape", default=None,
@@ -551,6 +606,10 @@ def main():
         run_case(args)
     elif args.ensemble_only and args.impl == "ours":
         run_ensemble_only(args)
+    elif args.learned_only and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_learned(args, torch.cuda.current_stream().cuda_stream)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -346,6 +346,83 @@ void lbm_batch_destroy(lbm_batch *b);
  * last lbm_batch_create failed (empty after a success). */
 const char *lbm_batch_last_error(const lbm_batch *b);
 
+/* ---- learned force correction ----------------------------------------------
+ * Not in the paper (an extension of its resolution study, Sec. 4): a small
+ * MLP predicts, from a particle's near-surface stencil at coarse resolution,
+ * the correction that brings the coarse run's hydrodynamic force and torque to
+ * those of a finely resolved run of the same method.
+ *
+ * Features (LBM_MLP_IN floats per particle):
+ *   [0,125)    solid indicator at a 5x5x5 grid of points X_p + (i-2, j-2,
+ *              k-2) h, h = (R + 2)/2, trilinear from cell centres (PSM:
+ *              min(sum_s eps_s, 1); MEM: 1 solid, 0 fluid);
+ *   [125,500)  (u - U_p)/u_ref at the same points (x, y, z blocks), u = j~/rho0
+ *              of the stored post-collision PDFs, body velocity in MEM solid
+ *              cells, 0 beyond a closed wall;
+ *   [500,512)  U_p/u_ref, Omega_p R/u_ref, F/(rho0 u_ref^2 D^2),
+ *              T/(rho0 u_ref^2 D^3), with F, T this step's hydrodynamic force.
+ * Outputs (LBM_MLP_OUT): (dF, dT) in the units of the last two blocks.
+ * Network: x^ = (x - mu)/sigma; h1 = tanh(W1 x^ + b1); h2 = tanh(W2 h1 + b2);
+ * y^ = W3 h2 + b3; y = y^ * s_out.  FP32 parameters, [in][out] layout:
+ * W1 (512x64), b1, W2 (64x64), b2, W3 (64x6), b3 (LBM_MLP_PARAMS floats).
+ * Normalisation block (LBM_MLP_NORM floats): mu[512], 1/sigma[512], s_out[6].
+ * Loss: L = 1/(2n) sum_s |y^_s - t_s / s_out|^2. */
+#define LBM_MLP_IN 512
+#define LBM_MLP_HIDDEN 64
+#define LBM_MLP_OUT 6
+#define LBM_MLP_PARAMS 37382
+#define LBM_MLP_NORM 1030
+
+typedef struct lbm_mlp lbm_mlp;
+
+/* Creates a model (parameters zero, identity normalisation) whose kernels run
+ * on `stream` (NULL: legacy default stream). */
+lbm_status lbm_mlp_create(void *stream, lbm_mlp **out);
+void lbm_mlp_destroy(lbm_mlp *m);
+const char *lbm_mlp_last_error(const lbm_mlp *m);
+
+/* Parameters / normalisation from or to host memory (count must equal
+ * LBM_MLP_PARAMS / LBM_MLP_NORM).  Setting parameters resets Adam's moments. */
+lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *host, size_t count);
+lbm_status lbm_mlp_get_params(lbm_mlp *m, float *host, size_t count);
+lbm_status lbm_mlp_set_normalization(lbm_mlp *m, const float *host, size_t count);
+lbm_status lbm_mlp_get_normalization(lbm_mlp *m, float *host, size_t count);
+
+/* Fits the normalisation to n samples on the device: mu and 1/sigma per input
+ * (sigma < 1e-6 -> 1), s_out = RMS of each target (floored at 1e-12).
+ * x_dev: n x LBM_MLP_IN floats; t_dev: n x LBM_MLP_OUT floats. */
+lbm_status lbm_mlp_fit_normalization(lbm_mlp *m, const float *x_dev, const float *t_dev, int n);
+
+/* y_dev (n x LBM_MLP_OUT) = MLP(x_dev) on the device (asynchronous). */
+lbm_status lbm_mlp_forward(lbm_mlp *m, const float *x_dev, int n, float *y_dev);
+
+/* Loss and parameter gradient dL/dP over n samples (FP32, samples summed in
+ * order: deterministic).  grad_host (LBM_MLP_PARAMS floats) and loss may be
+ * NULL; synchronises when either is given. */
+lbm_status lbm_mlp_gradient(lbm_mlp *m, const float *x_dev, const float *t_dev, int n,
+                            float *grad_host, size_t count, double *loss);
+
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr)
+ * on n samples; *loss (may be NULL) receives the loss at the parameters
+ * before the last update. */
+lbm_status lbm_mlp_train(lbm_mlp *m, const float *x_dev, const float *t_dev, int n, int steps,
+                         float lr, double *loss);
+
+/* Attaches a force model to a handle.  mode 0: off; 1: every step computes
+ * the features of each particle after the sweeps, evaluates m and adds the
+ * correction to the hydrodynamic force and torque before the rigid-body
+ * update (lbm_get_forces then returns the corrected values; a particle with
+ * a normalised feature beyond +-10, i.e. outside the training data, keeps its
+ * plain force); 2: features
+ * only (no correction; m may be NULL).  u_ref > 0 is the velocity scale of
+ * the features.  The model must live on the handle's device and stay alive
+ * while attached. */
+lbm_status lbm_set_force_model(lbm_handle *h, lbm_mlp *m, double u_ref, int mode);
+
+/* Features of the last step (n_particles x LBM_MLP_IN floats, host;
+ * synchronises).  count must equal n_particles * LBM_MLP_IN. */
+lbm_status lbm_get_features(lbm_handle *h, float *host, size_t count);
+
 #ifdef __cplusplus
 }
 #endif

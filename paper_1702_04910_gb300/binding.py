@@ -40,7 +40,12 @@ EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_eq
             "lbm_batch_create", "lbm_batch_step", "lbm_batch_autotune", "lbm_batch_set_tuning",
             "lbm_batch_get_particles", "lbm_batch_get_forces", "lbm_batch_get_pdf",
             "lbm_batch_cell_updates", "lbm_batch_device_bytes", "lbm_batch_graph_kernels",
-            "lbm_batch_synchronize", "lbm_batch_destroy", "lbm_batch_last_error")
+            "lbm_batch_synchronize", "lbm_batch_destroy", "lbm_batch_last_error",
+            "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_last_error", "lbm_mlp_set_params",
+            "lbm_mlp_get_params", "lbm_mlp_set_normalization", "lbm_mlp_get_normalization",
+            "lbm_mlp_fit_normalization", "lbm_mlp_forward", "lbm_mlp_gradient", "lbm_mlp_train",
+            "lbm_set_force_model", "lbm_get_features")
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS, MLP_NORM = 512, 64, 6, 37382, 1030
 BATCH_LAYOUTS = {"box32": 0, "box64": 1, "box128": 2, "plane": 3}
 
 
@@ -84,6 +89,7 @@ def load(build_if_missing: bool = True):
             _build.build()
         lib = ct.CDLL(path)
         vp, dp, i, sz = ct.c_void_p, ct.POINTER(ct.c_double), ct.c_int, ct.c_size_t
+        fp = ct.POINTER(ct.c_float)
         sig = {
             "lbm_create": (i, [ct.POINTER(LbmConfig), vp, ct.POINTER(vp)]),
             "lbm_set_particles": (i, [vp, i, ct.POINTER(LbmParticle)]),
@@ -116,6 +122,19 @@ def load(build_if_missing: bool = True):
             "lbm_batch_synchronize": (i, [vp]),
             "lbm_batch_destroy": (None, [vp]),
             "lbm_batch_last_error": (ct.c_char_p, [vp]),
+            "lbm_mlp_create": (i, [vp, ct.POINTER(vp)]),
+            "lbm_mlp_destroy": (None, [vp]),
+            "lbm_mlp_last_error": (ct.c_char_p, [vp]),
+            "lbm_mlp_set_params": (i, [vp, fp, sz]),
+            "lbm_mlp_get_params": (i, [vp, fp, sz]),
+            "lbm_mlp_set_normalization": (i, [vp, fp, sz]),
+            "lbm_mlp_get_normalization": (i, [vp, fp, sz]),
+            "lbm_mlp_fit_normalization": (i, [vp, vp, vp, i]),
+            "lbm_mlp_forward": (i, [vp, vp, i, vp]),
+            "lbm_mlp_gradient": (i, [vp, vp, vp, i, fp, sz, dp]),
+            "lbm_mlp_train": (i, [vp, vp, vp, i, i, ct.c_float, dp]),
+            "lbm_set_force_model": (i, [vp, vp, ct.c_double, i]),
+            "lbm_get_features": (i, [vp, fp, sz]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -327,6 +346,86 @@ def lbm_batch_destroy(b) -> None:
     load().lbm_batch_destroy(b)
 
 
+# ---- learned force correction (C names) ---------------------------------------------
+def _mcheck(m, st):
+    if st != LBM_OK:
+        msg = load().lbm_mlp_last_error(m)
+        raise LbmError(st, msg.decode() if msg else "")
+    return st
+
+
+def _fptr(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ct.POINTER(ct.c_float))
+
+
+def lbm_mlp_create(stream: int | None = None) -> ct.c_void_p:
+    m = ct.c_void_p()
+    st = load().lbm_mlp_create(ct.c_void_p(stream or 0), ct.byref(m))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_mlp_create failed")
+    return m
+
+
+def lbm_mlp_destroy(m) -> None:
+    load().lbm_mlp_destroy(m)
+
+
+def lbm_mlp_set_params(m, params: np.ndarray) -> None:
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _mcheck(m, load().lbm_mlp_set_params(m, _fptr(a), a.size))
+
+
+def lbm_mlp_get_params(m) -> np.ndarray:
+    a = np.empty(MLP_PARAMS, dtype=np.float32)
+    _mcheck(m, load().lbm_mlp_get_params(m, _fptr(a), a.size))
+    return a
+
+
+def lbm_mlp_set_normalization(m, norm: np.ndarray) -> None:
+    a = np.ascontiguousarray(norm, dtype=np.float32)
+    _mcheck(m, load().lbm_mlp_set_normalization(m, _fptr(a), a.size))
+
+
+def lbm_mlp_get_normalization(m) -> np.ndarray:
+    a = np.empty(MLP_NORM, dtype=np.float32)
+    _mcheck(m, load().lbm_mlp_get_normalization(m, _fptr(a), a.size))
+    return a
+
+
+def lbm_mlp_fit_normalization(m, x_ptr: int, t_ptr: int, n: int) -> None:
+    _mcheck(m, load().lbm_mlp_fit_normalization(m, ct.c_void_p(x_ptr), ct.c_void_p(t_ptr), int(n)))
+
+
+def lbm_mlp_forward(m, x_ptr: int, n: int, y_ptr: int) -> None:
+    _mcheck(m, load().lbm_mlp_forward(m, ct.c_void_p(x_ptr), int(n), ct.c_void_p(y_ptr)))
+
+
+def lbm_mlp_gradient(m, x_ptr: int, t_ptr: int, n: int):
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = ct.c_double()
+    _mcheck(m, load().lbm_mlp_gradient(m, ct.c_void_p(x_ptr), ct.c_void_p(t_ptr), int(n), _fptr(g),
+                                       g.size, ct.byref(loss)))
+    return g, loss.value
+
+
+def lbm_mlp_train(m, x_ptr: int, t_ptr: int, n: int, steps: int, lr: float) -> float:
+    loss = ct.c_double()
+    _mcheck(m, load().lbm_mlp_train(m, ct.c_void_p(x_ptr), ct.c_void_p(t_ptr), int(n), int(steps),
+                                    float(lr), ct.byref(loss)))
+    return loss.value
+
+
+def lbm_set_force_model(h, m, u_ref: float, mode: int) -> None:
+    _check(h, load().lbm_set_force_model(h, m, float(u_ref), int(mode)))
+
+
+def lbm_get_features(h, n: int) -> np.ndarray:
+    a = np.empty((n, MLP_IN), dtype=np.float32)
+    _check(h, load().lbm_get_features(h, _fptr(a), a.size))
+    return a
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 class Simulation:
     """One library handle; arrays are NumPy (host) unless noted."""
@@ -421,6 +520,14 @@ class Simulation:
     def synchronize(self):
         lbm_synchronize(self.h)
 
+    def set_force_model(self, model, u_ref, mode=1):
+        """model: an :class:`Mlp` (or None with mode 2: features only)."""
+        lbm_set_force_model(self.h, model.m if model is not None else None, u_ref, mode)
+        self._model = model  # keep it alive while attached
+
+    def features(self):
+        return lbm_get_features(self.h, self.np)
+
 
 class Batch:
     """A batched ensemble: ``cases`` are workload dicts with one particle each
@@ -484,3 +591,46 @@ class Batch:
 
     def synchronize(self):
         lbm_batch_synchronize(self.b)
+
+
+class Mlp:
+    """The force-correction network on the GPU (parameters, normalisation and
+    Adam state live on the device; data buffers are passed as device pointers)."""
+
+    def __init__(self, stream: int | None = None):
+        self.m = lbm_mlp_create(stream)
+
+    def close(self):
+        if getattr(self, "m", None):
+            lbm_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        lbm_mlp_set_params(self.m, p)
+
+    def params(self):
+        return lbm_mlp_get_params(self.m)
+
+    def set_normalization(self, nrm):
+        lbm_mlp_set_normalization(self.m, nrm)
+
+    def normalization(self):
+        return lbm_mlp_get_normalization(self.m)
+
+    def fit_normalization(self, x_ptr, t_ptr, n):
+        lbm_mlp_fit_normalization(self.m, x_ptr, t_ptr, n)
+
+    def forward(self, x_ptr, n, y_ptr):
+        lbm_mlp_forward(self.m, x_ptr, n, y_ptr)
+
+    def gradient(self, x_ptr, t_ptr, n):
+        return lbm_mlp_gradient(self.m, x_ptr, t_ptr, n)
+
+    def train(self, x_ptr, t_ptr, n, steps, lr):
+        return lbm_mlp_train(self.m, x_ptr, t_ptr, n, steps, lr)

@@ -71,6 +71,12 @@ struct lbm_handle {
     Coll<float> kf;
     Coll<dfloat> kff;
     Coll<fx64> kfx;
+    // learned force correction
+    lbm_mlp* model;
+    int model_mode;    // 0 off, 1 correct, 2 features only
+    double u_ref;
+    float* d_feat;     // [MAX_PARTICLES][LBM_MLP_IN]
+    float* d_corr;     // [MAX_PARTICLES][LBM_MLP_OUT]
     // profiling
     int profiling;
     std::vector<EventPair> events;
@@ -274,6 +280,22 @@ lbm_status step_once(lbm_handle* h) {
     int pi = prof_begin(h, PC_FINAL);
     CK(h, launch_finalize(L, nsub, h->d_force), "force total launch");
     prof_end(h, pi);
+    if (h->model_mode) {
+        // features of P^n and the flow after the sweeps; corrected force
+        pi = prof_begin(h, PC_OTHER);
+        CK(h, launch_features(h->storage, h->buf[h->cur], L, h->d_force, h->u_ref, h->d_feat),
+           "feature launch");
+        if (h->model_mode == 1) {
+            // a particle whose features lie beyond 10 standard deviations of
+            // the training data keeps the plain force (fallback)
+            CK(h, mlp_infer(h->model, h->d_feat, h->np, h->d_corr, 10.0f, h->stream),
+               "force model launch");
+            CK(h, launch_apply_correction(h->d_corr, h->d_parts, h->np, h->u_ref, h->cfg.rho0,
+                                          h->d_force, h->stream),
+               "force correction launch");
+        }
+        prof_end(h, pi);
+    }
     pi = prof_begin(h, PC_RIGID);
     CK(h, launch_rigid_body(L, h->d_force, h->cfg.gravity[0], h->cfg.gravity[1],
                             h->cfg.gravity[2], (double)nsub, h->cfg.wall_contact),
@@ -436,6 +458,8 @@ void lbm_destroy(lbm_handle* h) {
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
     cudaFree(h->d_status);
+    cudaFree(h->d_feat);
+    cudaFree(h->d_corr);
     free_particles(h);
     for (auto& p : h->events) {
         cudaEventDestroy(p.a);
@@ -660,6 +684,33 @@ lbm_status lbm_set_fields(lbm_handle* h, int what, const void* src, size_t bytes
 
 lbm_status lbm_synchronize(lbm_handle* h) {
     if (!h) return LBM_ERR_ARG;
+    return read_status(h);
+}
+
+lbm_status lbm_set_force_model(lbm_handle* h, lbm_mlp* m, double u_ref, int mode) {
+    if (!h) return LBM_ERR_ARG;
+    if (mode < 0 || mode > 2 || (mode == 1 && !m) || (mode != 0 && !(u_ref > 0.0)))
+        return fail(h, LBM_ERR_ARG, "mode 0..2; mode 1 needs a model; u_ref > 0");
+    if (mode && h->kind == 0) return fail(h, LBM_ERR_ARG, "a force model needs a coupling");
+    if (mode && !h->d_feat) {
+        CK(h, cudaMalloc(&h->d_feat, sizeof(float) * MAX_PARTICLES * LBM_MLP_IN), "cudaMalloc features");
+        CK(h, cudaMalloc(&h->d_corr, sizeof(float) * MAX_PARTICLES * LBM_MLP_OUT), "cudaMalloc features");
+        CK(h, cudaMemsetAsync(h->d_feat, 0, sizeof(float) * MAX_PARTICLES * LBM_MLP_IN, h->stream),
+           "memset");
+    }
+    h->model = mode == 1 ? m : nullptr;
+    h->model_mode = mode;
+    h->u_ref = u_ref;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_features(lbm_handle* h, float* host, size_t count) {
+    if (!h || !host) return LBM_ERR_ARG;
+    if (!h->d_feat) return fail(h, LBM_ERR_ARG, "no force model attached");
+    if (count != (size_t)h->np * LBM_MLP_IN) return fail(h, LBM_ERR_ARG, "count must be np * LBM_MLP_IN");
+    if (count == 0) return read_status(h);
+    CK(h, cudaMemcpyAsync(host, h->d_feat, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream),
+       "feature download");
     return read_status(h);
 }
 

@@ -387,7 +387,8 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
     }
     const int storage = cfgs[0].storage;
     if (storage != LBM_STORE_F64 && storage != LBM_STORE_F64_FX) {
-        std::snprintf(g_create_err, sizeof(g_create_err), "storage must be LBM_STORE_F64 or LBM_STORE_F64_FX");
+        std::snprintf(g_create_err, sizeof(g_create_err),
+                      "storage must be LBM_STORE_F64 or LBM_STORE_F64_FX");
         return LBM_ERR_UNSUPPORTED;
     }
     lbm_batch* b = new (std::nothrow) lbm_batch();

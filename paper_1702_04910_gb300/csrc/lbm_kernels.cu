@@ -943,30 +943,37 @@ __device__ __forceinline__ void bulk_segment(const double* __restrict__ src,
     store_own(dst, g, idx, f);
 }
 
+// One tile of case B in its bulk layout (see k_batch_bulk).
+template <typename C>
+__device__ __forceinline__ void batch_tile(const BatchCase& B, long long local) {
+    const int cur = B.cur;
+    if (B.layout == 1) {
+        const int nseg = (B.g.nx * B.g.ny + 255) / 256;
+        bulk_segment<C>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B), B.part->reg,
+                        (int)(local % nseg), (int)(local / nseg), threadIdx.x);
+    } else {
+        const int tX = (int)(local % B.g.ntx);
+        const int tY = (int)((local / B.g.ntx) % B.g.nty);
+        const int tZ = (int)(local / ((long long)B.g.ntx * B.g.nty));
+        bulk_tile<double, C, false, 1>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B), B.part, 1,
+                                       0, tX, tY, tZ, threadIdx.x % B.g.tx, threadIdx.x / B.g.tx);
+    }
+}
+
 // bulk sweep: persistent 256-thread blocks striding over the tiles of all
 // listed cases.  Each case has its own tiling (B.layout, chosen by the
 // autotuner): 0 box tiles of g.tx x g.ty cells (thread t -> (t mod g.tx,
-// t / g.tx)); 1 plane segments of 256 cells.
-template <typename C>
-__global__ void __launch_bounds__(256, BulkBlocks<C>::value)
+// t / g.tx)); 1 plane segments of 256 cells.  MODE: 0 FP64, 3 fixed-point
+// collision.
+template <int MODE>
+__global__ void __launch_bounds__(256, 3)
     k_batch_bulk(BatchCase* __restrict__ cases, BatchList l, long long total) {
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
         const int i = find_item(l.base, l.n, t);
         const BatchCase& B = cases[l.list[i]];
         const long long local = t - l.base[i];
-        const int cur = B.cur;
-        if (B.layout == 1) {
-            const int nseg = (B.g.nx * B.g.ny + 255) / 256;
-            bulk_segment<C>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B), B.part->reg,
-                            (int)(local % nseg), (int)(local / nseg), threadIdx.x);
-        } else {
-            const int tX = (int)(local % B.g.ntx);
-            const int tY = (int)((local / B.g.ntx) % B.g.nty);
-            const int tZ = (int)(local / ((long long)B.g.ntx * B.g.nty));
-            bulk_tile<double, C, false, 1>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B),
-                                           B.part, 1, 0, tX, tY, tZ, threadIdx.x % B.g.tx,
-                                           threadIdx.x / B.g.tx);
-        }
+        if (MODE == 3) batch_tile<fx64>(B, local);
+        else batch_tile<double>(B, local);
     }
 }
 
@@ -1253,9 +1260,9 @@ cudaError_t launch_batch_bulk(int mode, BatchCase* cases, BatchList l, long long
     if (l.n == 0 || total == 0) return cudaSuccess;
     const unsigned gsz = (unsigned)(grid <= 0 || total < grid ? total : grid);
     if (mode == 3)
-        k_batch_bulk<fx64><<<gsz, 256, 0, s>>>(cases, l, total);
+        k_batch_bulk<3><<<gsz, 256, 0, s>>>(cases, l, total);
     else
-        k_batch_bulk<double><<<gsz, 256, 0, s>>>(cases, l, total);
+        k_batch_bulk<0><<<gsz, 256, 0, s>>>(cases, l, total);
     return cudaGetLastError();
 }
 cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s) {
@@ -1280,9 +1287,9 @@ cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, 
 int batch_bulk_blocks_per_sm(int mode) {
     int nb = 0;
     if (mode == 3)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<fx64>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<3>, 256, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<double>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_bulk<0>, 256, 0);
     return nb > 0 ? nb : 1;
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "../../include/lbm_gb300.h"
 #include "lbm_device.cuh"
 #include "lbm_dfloat.cuh"
 #include "lbm_fixed.cuh"
@@ -173,6 +174,14 @@ cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, 
 cudaError_t launch_batch_init(BatchCase* cases, int n, long long max_cells, cudaStream_t s);
 int batch_bulk_blocks_per_sm(int mode);
 cudaError_t launch_map(const Launch& L);
+// learned force correction (lbm_learned.cu)
+cudaError_t launch_features(int storage, const void* state, const Launch& L, const double* force,
+                            double u_ref, float* feat);
+cudaError_t launch_apply_correction(const float* y, const DevParticle* parts, int np, double u_ref,
+                                    double rho0, double* force, cudaStream_t s);
+// clip > 0: samples with a normalised input beyond +-clip get y = 0
+cudaError_t mlp_infer(const lbm_mlp* m, const float* x, int n, float* y, float clip,
+                      cudaStream_t s);
 cudaError_t launch_rigid_body(const Launch& L, const double* force, double gx, double gy,
                               double gz, double dt, int wall_contact);
 

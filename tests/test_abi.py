@@ -100,7 +100,8 @@ def test_binding_wrapper_surface():
                  "synchronize", "close"):
         assert callable(getattr(binding.Simulation, name)), name
     for name in binding.EXPORTED:
-        if name not in ("lbm_last_error", "lbm_abi_version", "lbm_batch_last_error"):
+        if name not in ("lbm_last_error", "lbm_abi_version", "lbm_batch_last_error",
+                        "lbm_mlp_last_error"):
             assert callable(getattr(binding, name)), name
     for name in ("step", "autotune", "set_tuning", "particles", "forces", "pdf", "synchronize",
                  "close"):
