@@ -61,6 +61,12 @@
  *      the cell, a sample is inside iff |p - X_p| <= R (config: n = 4).
  * R16  Host-side particle replacement between steps (MEM): cells uncovered
  *      relative to the current mapping are set to f_eq(rho0, v).
+ * R27  Open z boundaries of the benchmark frame (Sec. 4.1), bc_z = 2: at the
+ *      bottom the velocity bounce-back of Eq. (12) with the inflow velocity
+ *      u_in; at the top the outflow of Sec. 4.1, f_qbar(x,t+1) = -f~_q(x,t)
+ *      + 2 f_eq,+_q(rho_out, u(x,t)), with f_eq,+ the even part of Eq. (3)
+ *      and u(x,t) the velocity of Eq. (8) of the boundary cell before the
+ *      stream.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -90,7 +96,8 @@ enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_UNSTABLE = -4,
 
 typedef struct {
     int nx, ny, nz;
-    int bc_z;          /* 0 periodic in z, 1 resting no-slip walls at z=0, nz */
+    int bc_z;          /* 0 periodic in z, 1 resting no-slip walls at z=0, nz,
+                          2 inflow at z=0 and outflow at z=nz (R27) */
     int collision;     /* ORC_BGK / ORC_TRT */
     int coupling;      /* ORC_PSM_* / ORC_MEM_* / ORC_NONE */
     double tau, magic; /* relaxation time, Lambda of Eq. (11) */
@@ -100,6 +107,8 @@ typedef struct {
     int subsample;     /* n of the n^3 supersampling (R15) */
     int subcycles;     /* LBM sweeps per global step (MEM: 2) */
     int wall_contact;  /* R13 */
+    double inflow[3];  /* bc_z = 2: inflow velocity at z = 0 (R27) */
+    double rho_out;    /* bc_z = 2: outflow density at z = nz (R27) */
 } orc_params;
 
 typedef struct {
@@ -298,6 +307,22 @@ static void map_particles(const orc_sim *s, int *solid) {
  * MEM solid cell are left for the boundary condition. */
 static void stream(orc_sim *s) {
     int mem = is_mem(s->p.coupling);
+    const int nxy = s->p.nx * s->p.ny;
+    double *uout = NULL;
+    if (s->p.bc_z == 2) {
+        /* R27: Eq. (8) velocity of the top-plane cells at time t, taken
+         * before the stream overwrites f */
+        uout = (double *)malloc(sizeof(double) * 3 * (size_t)nxy);
+        for (int y = 0; y < s->p.ny; ++y)
+            for (int x = 0; x < s->p.nx; ++x) {
+                long i = cell_index(s, x, y, s->p.nz - 1);
+                double fc[NQ], rho, U[3];
+                for (int q = 0; q < NQ; ++q) fc[q] = s->f[(long)q * s->n + i];
+                moments(fc, s->p.rho0, &rho, U);
+                for (int a = 0; a < 3; ++a)
+                    uout[3 * (x + s->p.nx * y) + a] = U[a] + s->p.fext[a] / (2.0 * s->p.rho0);
+            }
+    }
 #pragma omp parallel for
     for (int z = 0; z < s->p.nz; ++z)
         for (int y = 0; y < s->p.ny; ++y)
@@ -307,7 +332,26 @@ static void stream(orc_sim *s) {
                 for (int q = 0; q < NQ; ++q) {
                     long j = neighbour(s, x, y, z, CQ[q][0], CQ[q][1], CQ[q][2]);
                     if (j < 0) {
-                        s->f[(long)OPP[q] * s->n + i] = s->ft[(long)q * s->n + i];
+                        double v = s->ft[(long)q * s->n + i];
+                        if (s->p.bc_z == 2 && CQ[q][2] < 0) {
+                            /* inflow: velocity bounce-back, Eq. (12) with u_in */
+                            double cu = 0.0;
+                            for (int a = 0; a < 3; ++a) cu += CQ[q][a] * s->p.inflow[a];
+                            v = v - 2.0 * WQ[q] * s->p.rho0 * cu * INV_CS2;
+                        } else if (s->p.bc_z == 2) {
+                            /* outflow (R27) */
+                            const double *u = &uout[3 * (x + s->p.nx * y)];
+                            double cu = 0.0, uu = 0.0;
+                            for (int a = 0; a < 3; ++a) {
+                                cu += CQ[q][a] * u[a];
+                                uu += u[a] * u[a];
+                            }
+                            double feq_even = WQ[q] * (s->p.rho_out +
+                                                       s->p.rho0 * (0.5 * INV_CS2 * INV_CS2 * cu * cu -
+                                                                    0.5 * INV_CS2 * uu));
+                            v = -v + 2.0 * feq_even;
+                        }
+                        s->f[(long)OPP[q] * s->n + i] = v;
                     } else if (mem && s->solid[j]) {
                         /* handled by mem_boundary() */
                     } else {
@@ -315,6 +359,7 @@ static void stream(orc_sim *s) {
                     }
                 }
             }
+    free(uout);
 }
 
 /* Force/torque partials are kept per z plane so that the sum order does not
@@ -634,6 +679,7 @@ orc_sim *orc_create(const orc_params *p) {
     init_weights();
     if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || !(p->tau > 0.5)) return NULL;
     if (p->coupling < 0 || p->coupling > ORC_NONE) return NULL;
+    if (p->bc_z < 0 || p->bc_z > 2 || (p->bc_z == 2 && p->nz < 2)) return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
     if (s->p.subsample <= 0) s->p.subsample = 4;

@@ -39,7 +39,8 @@ class Params(ct.Structure):
                 ("tau", ct.c_double), ("magic", ct.c_double),
                 ("fext", ct.c_double * 3), ("gravity", ct.c_double * 3),
                 ("rho0", ct.c_double), ("subsample", ct.c_int),
-                ("subcycles", ct.c_int), ("wall_contact", ct.c_int)]
+                ("subcycles", ct.c_int), ("wall_contact", ct.c_int),
+                ("inflow", ct.c_double * 3), ("rho_out", ct.c_double)]
 
 
 class Particle(ct.Structure):
@@ -122,7 +123,8 @@ class Oracle:
 
     def __init__(self, shape, *, coupling="NONE", collision="TRT", tau=0.8,
                  magic=3.0 / 16.0, fext=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0),
-                 rho0=1.0, bc_z=0, subsample=4, subcycles=0, wall_contact=0):
+                 rho0=1.0, bc_z=0, subsample=4, subcycles=0, wall_contact=0,
+                 inflow=(0.0, 0.0, 0.0), rho_out=1.0):
         self._lib = _load()
         nx, ny, nz = (int(v) for v in shape)
         self.shape = (nx, ny, nz)
@@ -138,6 +140,9 @@ class Oracle:
             p.gravity[a] = float(gravity[a])
         p.rho0 = float(rho0)
         p.subsample, p.subcycles, p.wall_contact = int(subsample), int(subcycles), int(wall_contact)
+        for a in range(3):
+            p.inflow[a] = float(inflow[a])
+        p.rho_out = float(rho_out)
         self.params = p
         h = self._lib.orc_create(ct.byref(p))
         if not h:

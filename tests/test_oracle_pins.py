@@ -384,3 +384,54 @@ def test_fig1_drag_error(coupling):
     C = _drag_coefficient(coupling, tau)
     err = (C / 2.8402 - 1.0) * 100.0
     assert abs(err - ref) < 0.3, (coupling, err, ref)
+
+
+# ---- open z boundaries of the benchmark frame (Sec. 4.1) -----------------------------
+@pytest.mark.parametrize("collision", ["TRT", "BGK"])
+@pytest.mark.parametrize("u_in", [(0.0, 0.0, 0.05), (0.02, -0.01, 0.04)])
+def test_uniform_stream_is_a_fixed_point_of_inflow_and_outflow(collision, u_in):
+    """f_eq(rho_out, u_in) everywhere is steady under the inflow bounce-back
+    (Eq. (12) with u_in) at the bottom and the outflow condition at the top:
+    a sign or weight error in either boundary moves the state."""
+    shape = (6, 5, 12)
+    o = Oracle(shape, collision=collision, tau=0.7, bc_z=2, inflow=u_in, rho_out=1.0)
+    o.init_equilibrium(1.0, u_in)
+    f0 = o.pdf("pre")
+    o.step(25)
+    assert np.max(np.abs(o.pdf("pre") - f0)) < 1e-15
+    o.close()
+
+
+def test_resting_inflow_equals_a_resting_wall_below():
+    """With u_in = 0 the inflow boundary is the resting halfway bounce-back of
+    bc_z = 1: the two runs agree exactly wherever the top boundary has not yet
+    been felt (one cell per step)."""
+    c, w, _ = orc.lattice()
+    shape = (5, 4, 30)
+    f0 = W.perturbed_field(w, shape, 0.05, seed=3)
+    runs = []
+    for bc in (1, 2):
+        o = Oracle(shape, tau=0.8, bc_z=bc, inflow=(0.0, 0.0, 0.0), rho_out=1.0)
+        o.set_pdf(f0)
+        o.step(6)
+        runs.append(o.pdf("pre"))
+        o.close()
+    assert np.array_equal(runs[0][:, :30 - 8], runs[1][:, :30 - 8])
+    assert not np.array_equal(runs[0][:, -1], runs[1][:, -1])
+
+
+def test_outflow_relaxes_density_towards_rho_out():
+    """A fluid at rest at density 1.02 above a closed inflow (u_in = 0) drains
+    through the outflow (rho_out = 1): the mass decreases monotonically over
+    the first sound crossings and the top cell's density approaches rho_out."""
+    shape = (3, 3, 16)
+    o = Oracle(shape, tau=0.8, bc_z=2, inflow=(0.0, 0.0, 0.0), rho_out=1.0)
+    o.init_equilibrium(1.02)
+    masses = []
+    for _ in range(40):
+        o.step(1)
+        masses.append(o.pdf("pre").sum())
+    assert all(b < a for a, b in zip(masses, masses[1:]))
+    rho, _ = o.macro()
+    assert abs(rho[-1].mean() - 1.0) < abs(rho[0].mean() - 1.0)
+    o.close()
