@@ -98,7 +98,12 @@ typedef enum {
 
 typedef struct {
     int nx, ny, nz;            /* cells per axis, each >= 1                        */
-    int bc_z;                  /* 0: periodic in z; 1: resting no-slip walls      */
+    int bc_z;                  /* 0: periodic in z; 1: resting no-slip walls;     */
+                               /* 2: the open boundaries of Sec. 4.1: velocity    */
+                               /*    bounce-back (Eq. (12)) with `inflow` at      */
+                               /*    z = 0, outflow f_qbar = -f~_q + 2 f_eq,+_q(  */
+                               /*    rho_out, u) at z = nz; a particle must stay  */
+                               /*    R + 3 cells away from both (LBM_ERR_DOMAIN)  */
     int collision;             /* lbm_collision                                   */
     int coupling;              /* lbm_coupling                                    */
     double tau;                /* relaxation time, > 1/2 (nu = (tau - 1/2)/3)     */
@@ -110,6 +115,8 @@ typedef struct {
     int lbm_subcycles;         /* LBM sweeps per global step (0 -> 2 MEM, 1 PSM)  */
     int wall_contact;          /* 1: keep spheres one cell off closed z walls     */
     int storage;               /* lbm_storage                                     */
+    double inflow[3];          /* bc_z = 2: inflow velocity at z = 0              */
+    double rho_out;            /* bc_z = 2: outflow density at z = nz             */
 } lbm_config;
 
 /* Rigid spherical particle (Eq. (13) velocity field). */

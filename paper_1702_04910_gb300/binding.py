@@ -54,7 +54,8 @@ class LbmConfig(ct.Structure):
                 ("collision", ct.c_int), ("coupling", ct.c_int), ("tau", ct.c_double),
                 ("magic", ct.c_double), ("force_density", ct.c_double * 3),
                 ("gravity", ct.c_double * 3), ("rho0", ct.c_double), ("subsample", ct.c_int),
-                ("lbm_subcycles", ct.c_int), ("wall_contact", ct.c_int), ("storage", ct.c_int)]
+                ("lbm_subcycles", ct.c_int), ("wall_contact", ct.c_int), ("storage", ct.c_int),
+                ("inflow", ct.c_double * 3), ("rho_out", ct.c_double)]
 
 
 class LbmParticle(ct.Structure):
@@ -154,7 +155,8 @@ def _check(h, st):
 
 def make_config(shape, *, coupling="NONE", collision="TRT", tau=0.8, magic=3.0 / 16.0,
                 fext=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0), rho0=1.0, bc_z=0, subsample=4,
-                subcycles=0, wall_contact=0, storage="f64") -> LbmConfig:
+                subcycles=0, wall_contact=0, storage="f64", inflow=(0.0, 0.0, 0.0),
+                rho_out=1.0) -> LbmConfig:
     c = LbmConfig()
     c.nx, c.ny, c.nz = (int(v) for v in shape)
     c.bc_z = int(bc_z)
@@ -167,6 +169,9 @@ def make_config(shape, *, coupling="NONE", collision="TRT", tau=0.8, magic=3.0 /
     c.rho0 = float(rho0)
     c.subsample, c.lbm_subcycles, c.wall_contact = int(subsample), int(subcycles), int(wall_contact)
     c.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    for a in range(3):
+        c.inflow[a] = float(inflow[a])
+    c.rho_out = float(rho_out)
     return c
 
 

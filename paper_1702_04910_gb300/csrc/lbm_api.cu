@@ -358,7 +358,11 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     if (cfg->coupling < 0 || cfg->coupling > LBM_NONE) return LBM_ERR_ARG;
     if (cfg->collision != LBM_BGK && cfg->collision != LBM_TRT) return LBM_ERR_ARG;
     if (cfg->storage < LBM_STORE_F64 || cfg->storage > LBM_STORE_BF16S) return LBM_ERR_ARG;
-    if (cfg->bc_z != 0 && cfg->bc_z != 1) return LBM_ERR_ARG;
+    if (cfg->bc_z < 0 || cfg->bc_z > 2 || (cfg->bc_z == 2 && cfg->nz < 3)) return LBM_ERR_ARG;
+    if (cfg->bc_z == 2 &&
+        !(std::isfinite(cfg->inflow[0]) && std::isfinite(cfg->inflow[1]) && std::isfinite(cfg->inflow[2]) &&
+          cfg->rho_out > 0.0 && std::isfinite(cfg->rho_out)))
+        return LBM_ERR_ARG;
     if (cfg->subsample < 0 || cfg->subsample > 40 || cfg->lbm_subcycles < 0) return LBM_ERR_ARG;
     if (cfg->coupling == LBM_MEM_MR) return LBM_ERR_UNSUPPORTED;
     if (cfg->collision == LBM_TRT) {
@@ -406,6 +410,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     g.nz = cfg->nz;
     g.bc_z = cfg->bc_z;
     g.n = n;
+    set_open_boundaries(g, *cfg);
     g.tx = cfg->nx >= 128 ? 128 : (cfg->nx >= 64 ? 64 : 32);
     g.ty = 256 / g.tx;
     g.ntx = (cfg->nx + g.tx - 1) / g.tx;
@@ -485,8 +490,10 @@ lbm_status lbm_set_particles(lbm_handle* h, int n, const lbm_particle* host_in) 
         const double need = D + 2.0 * NEAR_HALO + 2.0;
         if (need > h->g.nx || need > h->g.ny || (!h->g.bc_z && need > h->g.nz))
             return fail(h, LBM_ERR_ARG, "particle diameter + 6 exceeds a periodic extent");
-        if (h->g.bc_z && (p.x[2] - 0.5 * D < 0.0 || p.x[2] + 0.5 * D > h->g.nz))
-            return fail(h, LBM_ERR_ARG, "particle crosses a closed wall");
+        const double margin = h->g.bc_z == 2 ? OPEN_MARGIN : 0.0;
+        if (h->g.bc_z && (p.x[2] - 0.5 * D - margin < 0.0 || p.x[2] + 0.5 * D + margin > h->g.nz))
+            return fail(h, LBM_ERR_ARG,
+                        "particle crosses a closed wall or comes within R + 3 of an open boundary");
         maxd = std::max(maxd, D);
     }
     const bool remap = h->have_particles && h->kind == 2 && n == h->np && n > 0;

@@ -299,6 +299,7 @@ lbm_status make_case(lbm_batch* b, int c, const lbm_config& cfg, const lbm_parti
     g.nz = cfg.nz;
     g.bc_z = cfg.bc_z;
     g.n = (long long)cfg.nx * cfg.ny * cfg.nz;
+    set_open_boundaries(g, cfg);
     set_tiling(g, LBM_BATCH_PLANE);
     const bool psm = cfg.coupling <= LBM_PSM_M3B2;
     k.kind = psm ? 1 : 2;

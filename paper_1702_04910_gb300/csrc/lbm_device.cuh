@@ -25,6 +25,10 @@ constexpr int NQ = 19;
 constexpr int MAX_PARTICLES = 32;   // particle records staged in shared memory
 constexpr int CELL_SLOTS = 2;       // objects that may touch one cell (Sec. 2.3, multi-object cells)
 constexpr double NEAR_HALO = 2.0;   // cells around a sphere handled by the coupling kernels
+// Distance a sphere surface keeps from an open z boundary (bc_z = 2): its
+// near region (R + NEAR_HALO) then never contains a boundary plane, so only
+// the plain pull needs the open-boundary rules.
+constexpr double OPEN_MARGIN = 3.0;
 
 // ---- D3Q19 velocity set (Sec. 2.1): rest, 6 axis, 12 diagonals in pairs ----
 __host__ __device__ constexpr int cx(int q) {
@@ -59,11 +63,17 @@ struct DevParticle {
 // one z plane.
 struct Geom {
     int nx, ny, nz;
-    int bc_z;           // 1: closed resting walls at z = 0 and z = nz
+    int bc_z;           // 1: closed resting walls at z = 0 and z = nz;
+                        // 2: inflow at z = 0, outflow at z = nz (Sec. 4.1)
     long long n;        // cells
     int tx, ty;         // tile extent in x, y (= block dims)
     int tz;             // z planes per tile (cells per thread along z in k_bulk)
     int ntx, nty, ntz;  // tiles per axis
+    // open z boundaries (bc_z = 2)
+    double uin[3];      // inflow velocity
+    double rho_out;     // outflow density
+    double rho0;        // reference density
+    double fhalf[3];    // f_ext / (2 rho0): Eq. (8) velocity = j~/rho0 - fhalf
 };
 
 // Collision constants in the arithmetic type C.
@@ -421,11 +431,52 @@ struct PullAll<T, C, NQ> {
                                                long long, C (&)[NQ]) {}
 };
 
+// Open z boundaries of the benchmark frame (bc_z = 2, Sec. 4.1).  PullAll has
+// put the resting halfway bounce-back value f~_qbar(x) on every link that
+// crosses z = 0 or z = nz.  Inflow (bottom): the moving-wall term of Eq. (12)
+// with u_in is added, f_q = f~_qbar(x) + 2 w_q rho0 (c_q . u_in) / c_s^2.
+// Outflow (top): f_q = -f~_qbar(x) + 2 f_eq,+_q(rho_out, u(x)), f_eq,+ the
+// even part of Eq. (3), u(x) the Eq. (8) velocity of the cell (its
+// post-collision momentum j~ = j + f_ext, so u = j~/rho0 - f_ext/(2 rho0)).
+template <typename T, typename C>
+__device__ __forceinline__ void open_boundaries(const T* __restrict__ src, const Geom& g,
+                                                const NbrOff& o, long long idx, C (&f)[NQ]) {
+    if (o.zlo) {
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) {
+            if (cz(q) <= 0) continue;
+            const double cu = cx(q) * g.uin[0] + cy(q) * g.uin[1] + cz(q) * g.uin[2];
+            f[q] = f[q] + (C)(6.0 * wq(q) * g.rho0 * cu);
+        }
+    }
+    if (o.zhi) {
+        double j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) {
+            const double v = ld_pdf(src + (long long)q * g.n + idx, q);
+            j[0] += v * cx(q);
+            j[1] += v * cy(q);
+            j[2] += v * cz(q);
+        }
+        double u[3];
+        for (int a = 0; a < 3; ++a) u[a] = j[a] / g.rho0 - g.fhalf[a];
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) {
+            if (cz(q) >= 0) continue;
+            const double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+            const double feq_even = wq(q) * (g.rho_out + g.rho0 * (4.5 * cu * cu - 1.5 * uu));
+            f[q] = (C)(2.0 * feq_even - (double)f[q]);
+        }
+    }
+}
+
 template <typename T, typename C>
 __device__ __forceinline__ void pull_plain(const T* __restrict__ src, const Geom& g, int x, int y,
                                            int z, long long idx, C (&f)[NQ]) {
     const NbrOff o = make_off(g, x, y, z);
     PullAll<T, C, 0>::run(src, g, o, idx, f);
+    if (g.bc_z == 2 && (o.zlo || o.zhi)) open_boundaries(src, g, o, idx, f);
 }
 
 template <typename T, typename C>

@@ -519,7 +519,11 @@ __device__ __forceinline__ void rigid_one(const Geom& g, DevParticle* __restrict
             if (P.x[a] < 0.0) P.x[a] += L[a];
             else if (P.x[a] >= L[a]) P.x[a] -= L[a];
         }
-        if (g.bc_z) {
+        if (g.bc_z == 2) {
+            // open boundaries: the near region must stay clear of them
+            if (P.x[2] - R - OPEN_MARGIN < 0.0 || P.x[2] + R + OPEN_MARGIN > L[2])
+                atomicOr(status, ST_DOMAIN);
+        } else if (g.bc_z) {
             if (wall_contact) {
                 if (P.x[2] - R < 1.0) {
                     P.x[2] = R + 1.0;

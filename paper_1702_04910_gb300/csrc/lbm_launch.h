@@ -133,6 +133,16 @@ inline Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) 
     return k;
 }
 
+// Open-boundary data of a configuration (bc_z = 2) into the geometry.
+inline void set_open_boundaries(Geom& g, const lbm_config& cfg) {
+    for (int a = 0; a < 3; ++a) {
+        g.uin[a] = cfg.bc_z == 2 ? cfg.inflow[a] : 0.0;
+        g.fhalf[a] = cfg.force_density[a] / (2.0 * cfg.rho0);
+    }
+    g.rho_out = cfg.bc_z == 2 ? cfg.rho_out : cfg.rho0;
+    g.rho0 = cfg.rho0;
+}
+
 // Status bits raised by kernels (OR-ed into *status).
 enum : int {
     ST_TOO_MANY_OBJECTS = 1,  // more than CELL_SLOTS particles touch a cell

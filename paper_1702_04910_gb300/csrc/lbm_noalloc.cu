@@ -80,7 +80,8 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
         return LBM_ERR_ARG;
     }
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || !(cfg->tau > 0.5) || !(cfg->rho0 > 0.0) ||
-        (cfg->bc_z != 0 && cfg->bc_z != 1) || cfg->coupling < 0 || cfg->coupling > LBM_NONE ||
+        cfg->bc_z < 0 || cfg->bc_z > 2 || (cfg->bc_z == 2 && (cfg->nz < 3 || !(cfg->rho_out > 0.0))) ||
+        cfg->coupling < 0 || cfg->coupling > LBM_NONE ||
         (cfg->collision != LBM_BGK && cfg->collision != LBM_TRT) || cfg->subsample < 0 ||
         cfg->subsample > 64) {
         set_err(err, err_len, "invalid configuration");
@@ -108,6 +109,7 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     g.nz = cfg->nz;
     g.bc_z = cfg->bc_z;
     g.n = (long long)cfg->nx * cfg->ny * cfg->nz;
+    set_open_boundaries(g, *cfg);
     g.tx = cfg->nx >= 128 ? 128 : (cfg->nx >= 64 ? 64 : 32);
     g.ty = 256 / g.tx;
     g.ntx = (cfg->nx + g.tx - 1) / g.tx;
@@ -119,8 +121,11 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     for (int i = 0; i < n; ++i) {
         const lbm_particle& p = particles_host[i];
         const double need = p.diameter + 2.0 * NEAR_HALO + 2.0;
+        const double margin = g.bc_z == 2 ? OPEN_MARGIN : 0.0;
         if (!(p.diameter >= 1.0) || !(p.density > 0.0) || need > g.nx || need > g.ny ||
-            (!g.bc_z && need > g.nz)) {
+            (!g.bc_z && need > g.nz) ||
+            (g.bc_z && (p.x[2] - 0.5 * p.diameter - margin < 0.0 ||
+                        p.x[2] + 0.5 * p.diameter + margin > g.nz))) {
             set_err(err, err_len, "particle diameter invalid for this lattice");
             return LBM_ERR_ARG;
         }

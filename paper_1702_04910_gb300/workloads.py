@@ -92,7 +92,11 @@ def sim_kwargs(case: dict) -> dict:
     """Solver keyword arguments of a workload dict (shared by both front ends)."""
     keys = ("coupling", "collision", "tau", "magic", "fext", "gravity", "rho0", "bc_z",
             "subsample", "subcycles", "wall_contact")
-    return {k: case[k] for k in keys}
+    kw = {k: case[k] for k in keys}
+    for k in ("inflow", "rho_out"):  # open boundaries of the benchmark frame
+        if k in case:
+            kw[k] = case[k]
+    return kw
 
 
 ENSEMBLE_COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI")

@@ -74,7 +74,8 @@ def test_struct_layouts_match_header():
     """Field order and sizes of the two public structs (x86-64 / aarch64 LP64)."""
     assert ct.sizeof(binding.LbmParticle) == 11 * 8 + 8
     assert binding.LbmConfig.tau.offset == 24
-    assert binding.LbmConfig.storage.offset == 108 and ct.sizeof(binding.LbmConfig) == 112
+    assert binding.LbmConfig.storage.offset == 108 and binding.LbmConfig.inflow.offset == 112
+    assert binding.LbmConfig.rho_out.offset == 136 and ct.sizeof(binding.LbmConfig) == 144
     text = header_text()
     cfg_block = text[text.index("typedef struct {"):text.index("} lbm_config;")]
     fields = re.findall(r"\b(?:int|double)\s+([a-z_0-9\[\], ]+);", cfg_block)

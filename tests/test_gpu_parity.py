@@ -291,3 +291,45 @@ def test_particle_leaving_through_a_wall_is_reported():
         g.forces()
     assert ei.value.status == LBM_ERR_DOMAIN
     g.synchronize()  # status cleared, context intact
+
+
+# ---- open z boundaries of the benchmark frame (Sec. 4.1, bc_z = 2) -----------------------
+@pytest.mark.parametrize("storage", ["f64", "f64fx", "f64ff"])
+def test_open_boundaries_parity(lattice, storage):
+    """Fluid-only channel with the inflow bounce-back below and the outflow
+    above, started from a perturbed stream."""
+    _, w, _ = lattice
+    shape = (12, 10, 24)
+    kw = dict(coupling="NONE", collision="TRT", tau=0.62, bc_z=2, inflow=(0.01, 0.0, 0.05),
+              rho_out=1.0)
+    o = Oracle(shape, **kw)
+    from paper_1702_04910_gb300.binding import Simulation
+    g = Simulation(shape, storage=storage, **kw)
+    f0 = W.perturbed_field(w, shape, 0.03, seed=9)
+    o.set_pdf(f0)
+    g.set_pdf_pre(f0)
+    o.step(30)
+    g.step(30)
+    compare_pdf(o, g)
+    g.close()
+    o.close()
+
+
+@pytest.mark.parametrize("coupling,collision", [("PSM_M2B2", "BGK"), ("PSM_M1B1", "BGK"),
+                                                ("MEM_CLI", "TRT"), ("MEM_BB", "TRT")])
+def test_frame_fixed_sphere_parity(lattice, coupling, collision):
+    """A fixed sphere in the inflow/outflow frame (5.34D x 5.34D x 16D at D = 6)."""
+    case = {"shape": (32, 32, 96), "bc_z": 2, "coupling": coupling, "collision": collision,
+            "tau": 0.53, "magic": 3.0 / 16.0, "fext": (0.0, 0.0, 0.0), "gravity": (0.0, 0.0, 0.0),
+            "rho0": 1.0, "subsample": 4, "subcycles": 2 if coupling.startswith("MEM") else 1,
+            "wall_contact": 0, "inflow": (0.0, 0.0, 0.04), "rho_out": 1.0,
+            "particles": [{"x": (16.02, 16.02, 32.04), "u": (0, 0, 0), "omega": (0, 0, 0),
+                           "diameter": 6.0, "density": 1.5, "fixed": 1}]}
+    o, g = make_pair(case)
+    start(o, g, lattice, u=(0.0, 0.0, 0.04))
+    o.step(25)
+    g.step(25)
+    compare_pdf(o, g)
+    compare_forces(o, g)
+    g.close()
+    o.close()
