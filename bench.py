@@ -35,10 +35,11 @@ METRIC = "MLUPS and % of HBM roofline, coupled D3Q19 step; force/velocity error 
 # k_bulk with FP64 arithmetic is bound by the FP64 pipe (2 FP64 lane-operations
 # per SM per cycle on GB300, ncu peak_sustained): its roofline counts FP64
 # thread-instructions per cell update, measured by ncu on the 128x128x256
-# settling case (profiles/k_bulk_f64_settling_128x128x256.md), and the DRAM
-# bytes per cell update of the same capture (None once the kernel changes).
-K_BULK_F64_DP_INST_PER_CELL = 124.2
-K_BULK_F64_DRAM_BYTES_PER_CELL = None
+# settling case (profiles/k_bulk_f64_settling_128x128x256.md, per cell the
+# kernel updates), and the DRAM bytes per cell update of the same capture
+# (set to None whenever the kernel changes).
+K_BULK_F64_DP_INST_PER_CELL = 127.0
+K_BULK_F64_DRAM_BYTES_PER_CELL = 292.6
 FP64_LANE_OPS_PER_SM_CLK = 2
 COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI")
 SHAPE = (128, 128, 512)
@@ -456,6 +457,8 @@ def run_ours(args):
                        "replicas_per_rank": 1},
             "roofline": roofline,
             "kernel_time_share": {k: (v / tot if tot else 0.0) for k, v in share.items()},
+            "kernel_time_share_note": "CUDA-event time per class; the near sweep runs on its own "
+                                      "stream beside the bulk sweep, so its time includes the overlap",
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d // args.steps,
                     "d2h_bytes_per_step": d2h // args.steps,
                     "path": "C ABI per step: lbm_get_particles/lbm_set_particles (host), lbm_step, lbm_get_forces (host)"},
