@@ -281,6 +281,132 @@ __global__ void __launch_bounds__(256, BulkBlocks<C>::value)
 }
 
 // ---------------------------------------------------------------------------
+// 16-bit shifted storage, two x-neighbours per thread.  The pair (x0, x0 + 1),
+// x0 even, is read and written as one 32-bit word per direction (nx even, so
+// every row starts on a 4-byte boundary); a pull across x takes the two
+// aligned words around the shifted pair and selects its halves with a byte
+// permute.  Conversions use the packed two-value forms.  The arithmetic per
+// cell is exactly that of k_bulk (same FP32 operations, same roundings).
+template <typename T> struct Pair16;
+template <>
+struct Pair16<__half> {
+    __device__ __forceinline__ static float2 unpack(unsigned u) {
+        __half2 h;
+        memcpy(&h, &u, 4);
+        return __half22float2(h);
+    }
+    __device__ __forceinline__ static unsigned pack(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        unsigned u;
+        memcpy(&u, &h, 4);
+        return u;
+    }
+};
+template <>
+struct Pair16<__nv_bfloat16> {
+    __device__ __forceinline__ static float2 unpack(unsigned u) {
+        __nv_bfloat162 h;
+        memcpy(&h, &u, 4);
+        return __bfloat1622float2(h);
+    }
+    __device__ __forceinline__ static unsigned pack(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        unsigned u;
+        memcpy(&u, &h, 4);
+        return u;
+    }
+};
+
+__device__ __forceinline__ unsigned ld_word(const void* p) {
+    return __ldg(reinterpret_cast<const unsigned*>(p));
+}
+
+// direction Q of the pair at row `row` (= lin(0, y, z)); xm2 / xp2 are the
+// (periodic) even columns left / right of x0
+template <typename T, int Q>
+__device__ __forceinline__ void pull_pair_one(const T* __restrict__ src, const Geom& g,
+                                              const NbrOff& o, long long row, int x0, int xm2,
+                                              int xp2, float (&fa)[NQ], float (&fb)[NQ]) {
+    const float w = (float)wq(Q);
+    float2 v;
+    if ((cz(Q) > 0 && o.zlo) || (cz(Q) < 0 && o.zhi)) {
+        v = Pair16<T>::unpack(ld_word(src + (long long)opp(Q) * g.n + row + x0));  // halfway BB
+    } else {
+        long long r = row;
+        if (cy(Q) > 0) r += o.dym;
+        else if (cy(Q) < 0) r += o.dyp;
+        if (cz(Q) > 0) r += o.dzm;
+        else if (cz(Q) < 0) r += o.dzp;
+        const T* a = src + (long long)Q * g.n + r;
+        if (cx(Q) == 0) {
+            v = Pair16<T>::unpack(ld_word(a + x0));
+        } else if (cx(Q) > 0) {  // cells x0 - 1, x0
+            v = Pair16<T>::unpack(__byte_perm(ld_word(a + xm2), ld_word(a + x0), 0x5432));
+        } else {  // cells x0 + 1, x0 + 2
+            v = Pair16<T>::unpack(__byte_perm(ld_word(a + x0), ld_word(a + xp2), 0x5432));
+        }
+    }
+    fa[Q] = v.x + w;
+    fb[Q] = v.y + w;
+}
+
+template <typename T, int Q>
+struct PullPair {
+    __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
+                                               const NbrOff& o, long long row, int x0, int xm2,
+                                               int xp2, float (&fa)[NQ], float (&fb)[NQ]) {
+        pull_pair_one<T, Q>(src, g, o, row, x0, xm2, xp2, fa, fb);
+        PullPair<T, Q + 1>::run(src, g, o, row, x0, xm2, xp2, fa, fb);
+    }
+};
+template <typename T>
+struct PullPair<T, NQ> {
+    __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const NbrOff&,
+                                               long long, int, int, int, float (&)[NQ],
+                                               float (&)[NQ]) {}
+};
+
+// Grid (ceil(nx / (2 PAIR_TX)), ceil(ny / PAIR_TY), nz), block (PAIR_TX, PAIR_TY).
+constexpr int PAIR_TX = 64, PAIR_TY = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
+    k_bulk_pair(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<float> k,
+                const DevParticle* __restrict__ parts, int np) {
+    const int x0 = 2 * (blockIdx.x * PAIR_TX + threadIdx.x);
+    const int y = blockIdx.y * PAIR_TY + threadIdx.y, z = blockIdx.z;
+    if (x0 >= g.nx || y >= g.ny) return;
+    bool near_a = false, near_b = false;  // k_near's cells are left alone
+    for (int s = 0; s < np; ++s) {
+        near_a = near_a || cell_in_reg(g, parts[s].reg, x0, y, z);
+        near_b = near_b || cell_in_reg(g, parts[s].reg, x0 + 1, y, z);
+    }
+    if (near_a && near_b) return;
+    const NbrOff o = make_off(g, x0, y, z);
+    const long long row = lin(g, 0, y, z);
+    const int xm2 = x0 == 0 ? g.nx - 2 : x0 - 2;
+    const int xp2 = x0 + 2 == g.nx ? 0 : x0 + 2;
+    float fa[NQ], fb[NQ];
+    PullPair<T, 0>::run(src, g, o, row, x0, xm2, xp2, fa, fb);
+    collide_fluid(fa, k);
+    collide_fluid(fb, k);
+    if (!near_a && !near_b) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float w = (float)wq(q);
+            *reinterpret_cast<unsigned*>(dst + (long long)q * g.n + row + x0) =
+                Pair16<T>::pack(fa[q] - w, fb[q] - w);
+        }
+    } else {
+        const long long idx = row + x0 + (near_a ? 1 : 0);
+        const float(&f)[NQ] = near_a ? fb : fa;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            dst[(long long)q * g.n + idx] = PdfStore<T>::template save<float>(f[q], q);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // near-particle sweep over the cell region of each particle (cells within
 // R + NEAR_HALO of the centre per axis).  Grid (bx, by, bz * np) of
 // NEAR_BX x NEAR_BY x NEAR_BZ blocks: block (bx, by, bz) of particle p covers
@@ -1059,6 +1185,17 @@ cudaError_t bulk_cpt(const void* src, void* dst, const Launch& L) {
 // 16/32-bit sweeps are memory bound and take two z cells per thread.
 template <typename T, typename C = T>
 cudaError_t bulk_t(const void* src, void* dst, const Launch& L) {
+    if constexpr (sizeof(T) == 2) {
+        // 16-bit sweep with two x-neighbours per thread: even nx, streaming,
+        // no open boundaries (those planes take the per-cell kernel)
+        if (!L.nostream && L.g.nx % 2 == 0 && L.g.bc_z != 2) {
+            dim3 grid((L.g.nx + 2 * PAIR_TX - 1) / (2 * PAIR_TX), (L.g.ny + PAIR_TY - 1) / PAIR_TY,
+                      L.g.nz);
+            k_bulk_pair<T><<<grid, dim3(PAIR_TX, PAIR_TY, 1), 0, L.stream>>>(
+                (const T*)src, (T*)dst, L.g, L.kf, L.parts, L.all_tiles ? 0 : L.cp.np);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (sizeof(T) <= 4) {
         if (L.g.tz == 2) return bulk_cpt<T, C, 2>(src, dst, L);
     }
