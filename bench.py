@@ -236,6 +236,36 @@ def run_learned(args, stream):
     }
 
 
+def run_frame_study(args):
+    """Case A of the paper's benchmark frame (Sec. 4.1) at diameter --frame."""
+    import torch
+
+    from paper_1702_04910_gb300 import frame
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                          "tab1_ga144_upv.txt")
+    table = {}
+    with open(golden) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                c, d, u = line.split()
+                table[(c, int(d))] = float(u)
+    out = {}
+    for coupling in ("MEM_BB", "MEM_CLI", "PSM_M1B1", "PSM_M2B2"):
+        t0 = time.perf_counter()
+        r = frame.run_frame(D=args.frame, coupling=coupling, storage="f64fx", stream=stream)
+        paper = table.get((coupling, int(round(args.frame))))
+        out[coupling] = {"u_pV": r["u_pV"], "u_pV_paper_tab1": paper,
+                         "rel_diff_vs_paper": (abs(r["u_pV"] - paper) / abs(paper)) if paper else None,
+                         "Ga": r["calibration"][-1]["Ga"], "nu": r["nu"],
+                         "calibration_steps": r["calibration_steps"], "free_steps": r["free_steps"],
+                         "seconds": time.perf_counter() - t0}
+    print(json.dumps({"frame": "case A, Ga = 144", "D": args.frame, "shape": frame.frame_shape(args.frame),
+                      "results": out}), flush=True)
+
+
 def run_ensemble_only(args):
     import torch
     torch.cuda.set_device(0)
@@ -595,6 +625,9 @@ def main():
     ap.add_argument("--learned", choices=("small", "full", "none"), default="small",
                     help="learned force correction study reported as a variant")
     ap.add_argument("--learned-only", action="store_true")
+    ap.add_argument("--frame", type=float, default=None, metavar="D",
+                    help="run the paper's benchmark frame (case A, Ga = 144) at diameter D for "
+                         "MEM BB/CLI and PSM M1B1/M2B2 and print u_pV against the paper's Tab. 1")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the settling workload by this factor in every length (tests)")
     ap.add_argument("--case-shape", default=None,
@@ -609,6 +642,8 @@ def main():
         run_case(args)
     elif args.ensemble_only and args.impl == "ours":
         run_ensemble_only(args)
+    elif args.frame is not None and args.impl == "ours":
+        run_frame_study(args)
     elif args.learned_only and args.impl == "ours":
         import torch
         torch.cuda.set_device(0)
