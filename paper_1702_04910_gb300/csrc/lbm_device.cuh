@@ -646,6 +646,40 @@ __device__ inline int solid_count(const Geom& g, const DevParticle& P, int x, in
     return inside;
 }
 
+// solid_count with the n^3 samples spread over the 32 lanes of a warp: every
+// lane passes the same cell; all lanes must call it (warp-synchronous).  Same
+// predicate and the same integer count as solid_count.
+__device__ inline int solid_count_warp(const Geom& g, const DevParticle& P, int x, int y, int z,
+                                       int n, int lane) {
+    const bool pow2 = (n & (n - 1)) == 0;
+    const double h = 0.5 / n;
+    const double X = x, Y = y, Z = z;
+    int inside = 0;
+    for (int s = lane; s < n * n * n; s += 32) {
+        const int i = s % n, j = (s / n) % n, k = s / (n * n);
+        const double pz = Z + (pow2 ? (2 * k + 1) * h : (k + 0.5) / n);
+        const double py = Y + (pow2 ? (2 * j + 1) * h : (j + 0.5) / n);
+        const double px = X + (pow2 ? (2 * i + 1) * h : (i + 0.5) / n);
+        inside += point_inside(g, P, px, py, pz) ? 1 : 0;
+    }
+    return __reduce_add_sync(0xffffffffu, inside);
+}
+
+// The quick part of solid_count: 0 or n^3 for cells wholly outside / inside
+// the sphere, -1 for cells that need the samples.
+__device__ inline int solid_count_quick(const Geom& g, const DevParticle& P, int x, int y, int z,
+                                        int n) {
+    double dx, dy, dz;
+    separation(g, x + 0.5, y + 0.5, z + 0.5, P, dx, dy, dz);
+    double ax = fabs(dx), ay = fabs(dy), az = fabs(dz);
+    double nxd = fmax(ax - 0.5, 0.0), nyd = fmax(ay - 0.5, 0.0), nzd = fmax(az - 0.5, 0.0);
+    double R2 = mul_rn(P.r, P.r);
+    if (norm2_rn(nxd, nyd, nzd) > R2 * (1.0 + 1e-12) + 1e-9) return 0;
+    double fxd = ax + 0.5, fyd = ay + 0.5, fzd = az + 0.5;
+    if (norm2_rn(fxd, fyd, fzd) < R2 * (1.0 - 1e-12) - 1e-9) return n * n * n;
+    return -1;
+}
+
 __device__ inline double solid_fraction(const Geom& g, const DevParticle& P, int x, int y, int z,
                                         int n) {
     return (double)solid_count(g, P, x, y, z, n) / ((double)n * n * n);

@@ -285,8 +285,13 @@ __global__ void __launch_bounds__(256, BulkBlocks<C>::value)
 // x0 even, is read and written as one 32-bit word per direction (nx even, so
 // every row starts on a 4-byte boundary); a pull across x takes the two
 // aligned words around the shifted pair and selects its halves with a byte
-// permute.  Conversions use the packed two-value forms.  The arithmetic per
-// cell is exactly that of k_bulk (same FP32 operations, same roundings).
+// permute.  Conversions use the packed two-value forms.  The collision runs on
+// the stored shifted values g_q = f_q - w_q themselves: with rho = 1 + sum_q
+// g_q and j = sum_q g_q c_q (sum_q w_q c_q = 0), the folded update
+// f' = alpha f + beta fbar - (P +- M) becomes g' = alpha g + beta gbar -
+// (P +- M) with rho replaced by sum_q g_q in P (alpha + beta - 1 = lambda_+
+// cancels the l+ w_q term), so the same collide_fluid code applies with no
+// shift on load or store, and FP32 rounds the small deviations, not f.
 template <typename T> struct Pair16;
 template <>
 struct Pair16<__half> {
@@ -301,6 +306,7 @@ struct Pair16<__half> {
         memcpy(&u, &h, 4);
         return u;
     }
+    __device__ __forceinline__ static __half one(float a) { return __float2half_rn(a); }
 };
 template <>
 struct Pair16<__nv_bfloat16> {
@@ -315,6 +321,7 @@ struct Pair16<__nv_bfloat16> {
         memcpy(&u, &h, 4);
         return u;
     }
+    __device__ __forceinline__ static __nv_bfloat16 one(float a) { return __float2bfloat16_rn(a); }
 };
 
 __device__ __forceinline__ unsigned ld_word(const void* p) {
@@ -327,7 +334,6 @@ template <typename T, int Q>
 __device__ __forceinline__ void pull_pair_one(const T* __restrict__ src, const Geom& g,
                                               const NbrOff& o, long long row, int x0, int xm2,
                                               int xp2, float (&fa)[NQ], float (&fb)[NQ]) {
-    const float w = (float)wq(Q);
     float2 v;
     if ((cz(Q) > 0 && o.zlo) || (cz(Q) < 0 && o.zhi)) {
         v = Pair16<T>::unpack(ld_word(src + (long long)opp(Q) * g.n + row + x0));  // halfway BB
@@ -346,8 +352,8 @@ __device__ __forceinline__ void pull_pair_one(const T* __restrict__ src, const G
             v = Pair16<T>::unpack(__byte_perm(ld_word(a + x0), ld_word(a + xp2), 0x5432));
         }
     }
-    fa[Q] = v.x + w;
-    fb[Q] = v.y + w;
+    fa[Q] = v.x;  // shifted values g_q (see above)
+    fb[Q] = v.y;
 }
 
 template <typename T, int Q>
@@ -392,17 +398,14 @@ __global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
     collide_fluid(fb, k);
     if (!near_a && !near_b) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const float w = (float)wq(q);
+        for (int q = 0; q < NQ; ++q)
             *reinterpret_cast<unsigned*>(dst + (long long)q * g.n + row + x0) =
-                Pair16<T>::pack(fa[q] - w, fb[q] - w);
-        }
+                Pair16<T>::pack(fa[q], fb[q]);
     } else {
         const long long idx = row + x0 + (near_a ? 1 : 0);
         const float(&f)[NQ] = near_a ? fb : fa;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q)
-            dst[(long long)q * g.n + idx] = PdfStore<T>::template save<float>(f[q], q);
+        for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + idx] = Pair16<T>::one(f[q]);
     }
 }
 
@@ -537,19 +540,37 @@ __global__ void __launch_bounds__(256)
 // PSM: the number of the n^3 supersamples inside particle p (R15).  The
 // sweeps then read these instead of re-evaluating FP64 geometry per link.
 // Grid (ceil(ex/32), ey, ez * np), 32 threads per block.
+// Called by all 32 lanes of a warp that covers 32 consecutive kx of one row
+// (ky, kz the same on every lane).  PSM: cells wholly outside or inside the
+// sphere take the quick count; the warp then samples each remaining cell of
+// the row together (two of the 64 samples per lane for n = 4), so a row costs
+// a few cooperative sample sets instead of one 64-sample loop per lane.
 template <int KIND>
 __device__ __forceinline__ void map_cell(const Geom& g, const Coupl& cp, const DevParticle* sp,
                                          unsigned short* __restrict__ map, int ex, int ey, int ez,
                                          int p, int kx, int ky, int kz) {
     const int* R = sp[p].reg;
-    if (kx >= R[1] || ky >= R[5] || kz >= R[9]) return;
+    const bool valid = kx < R[1] && ky < R[5] && kz < R[9];
     int x = R[0] + kx, y = R[4] + ky, z = R[8] + kz;
     if (x >= g.nx) x -= g.nx;
     if (y >= g.ny) y -= g.ny;
     if (z >= g.nz) z -= g.nz;
-    const int v = KIND == 2 ? cell_owner(g, sp, cp.np, x, y, z)
-                            : solid_count(g, sp[p], x, y, z, cp.subsample);
-    map[(((long long)p * ez + kz) * ey + ky) * ex + kx] = (unsigned short)v;
+    unsigned short* out = map + (((long long)p * ez + kz) * ey + ky) * ex + kx;
+    if (KIND == 2) {
+        if (valid) *out = (unsigned short)cell_owner(g, sp, cp.np, x, y, z);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int quick = valid ? solid_count_quick(g, sp[p], x, y, z, cp.subsample) : 0;
+    if (valid && quick >= 0) *out = (unsigned short)quick;
+    unsigned todo = __ballot_sync(0xffffffffu, valid && quick < 0);
+    while (todo) {
+        const int c = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int xc = __shfl_sync(0xffffffffu, x, c);
+        const int cnt = solid_count_warp(g, sp[p], xc, y, z, cp.subsample, lane);
+        if (lane == c) *out = (unsigned short)cnt;
+    }
 }
 
 template <int KIND>
