@@ -323,6 +323,8 @@ lbm_status read_status(lbm_handle* h) {
     if (st) {
         CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream), "status reset");
         if (st & ST_DOMAIN) return fail(h, LBM_ERR_DOMAIN, "a particle left the domain through a closed wall");
+        if (st & ST_BOUNDS)
+            return fail(h, LBM_ERR_CUDA, "an index check in a coupling kernel failed; the step is invalid");
         if (st & ST_UNSTABLE)
             return fail(h, LBM_ERR_UNSTABLE,
                         "a particle state became non-finite or moved a cell or more per step");
@@ -382,7 +384,12 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     h->stream = (cudaStream_t)stream;
     cudaGetDevice(&h->device);
     {
-        cudaError_t e0 = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        // the near sweep's stream has the highest priority: its few long-lived
+        // blocks are placed as soon as k_bulk blocks retire, instead of
+        // waiting behind the whole bulk grid
+        int lo_prio = 0, hi_prio = 0;
+        cudaError_t e0 = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        if (e0 == cudaSuccess) e0 = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi_prio);
         if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
         if (e0 != cudaSuccess) {

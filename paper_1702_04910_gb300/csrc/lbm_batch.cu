@@ -240,6 +240,8 @@ lbm_status read_status(lbm_batch* b) {
     if (st) {
         BK(b, cudaMemsetAsync(b->dstatus, 0, sizeof(int), b->stream), "status reset");
         if (st & ST_DOMAIN) return fail(b, LBM_ERR_DOMAIN, "a particle left the domain through a closed wall");
+        if (st & ST_BOUNDS)
+            return fail(b, LBM_ERR_CUDA, "an index check in a coupling kernel failed; the step is invalid");
         if (st & ST_UNSTABLE)
             return fail(b, LBM_ERR_UNSTABLE,
                         "a particle state became non-finite or moved a cell or more per step");
@@ -485,7 +487,9 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
     b->arena_bytes = off;
 
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    int lo_prio = 0, hi_prio = 0;  // near-sweep branch first in line (see lbm_api.cu)
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi_prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->t0);

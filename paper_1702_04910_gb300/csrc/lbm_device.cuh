@@ -701,7 +701,12 @@ __device__ __forceinline__ bool region_offsets(const Geom& g, const int* r, int 
     return ox < r[1] && oy < r[5] && oz < r[9];
 }
 
+// Offsets outside the map read as 0 (fluid / uncovered) without touching
+// memory; callers only pass offsets inside a region box.
 __device__ __forceinline__ unsigned short map_at(const GeoMap& m, int s, int ox, int oy, int oz) {
+    if (s < 0 || s >= MAX_PARTICLES || ox < 0 || ox >= m.ex || oy < 0 || oy >= m.ey || oz < 0 ||
+        oz >= m.ez)
+        return 0;
     return __ldg(m.map + (((long long)s * m.ez + oz) * m.ey + oy) * m.ex + ox);
 }
 

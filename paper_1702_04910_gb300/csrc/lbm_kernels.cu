@@ -97,8 +97,19 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
         return;
     }
     const int owner = owner_of(g, parts, np, gm, xs, ys, zs);
+    // index checks: a failure is reported (ST_BOUNDS) and the access skipped
     if (!owner) {
+        if (xs < 0 || xs >= g.nx || ys < 0 || ys >= g.ny || zs < 0 || zs >= g.nz) {
+            atomicOr(status, ST_BOUNDS);
+            f[Q] = (C)0.0;
+            return;
+        }
         f[Q] = PdfStore<T>::template load<C>(src + (long long)Q * g.n + lin(g, xs, ys, zs), Q);
+        return;
+    }
+    if (owner < 0 || owner > np) {
+        atomicOr(status, ST_BOUNDS);
+        f[Q] = (C)0.0;
         return;
     }
     const DevParticle& P = parts[owner - 1];
@@ -443,6 +454,10 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
             if (cell_in_reg(g, sp[s].reg, x, y, z)) active = false;
     Slots slots;
     slots.clear();
+    if (active && (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)) {
+        atomicOr(status, ST_BOUNDS);
+        active = false;
+    }
     if (active) {
         const long long idx = lin(g, x, y, z);
         C f[NQ];
@@ -502,7 +517,8 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
         if (tid < 6) {
             double acc = 0.0;
             for (int w = 0; w < nwarp; ++w) acc += red[w][tid];
-            partials[(((long long)p * nblk + blk) * cp.np + q) * 6 + tid] = acc;
+            if (p < cp.np && blk < nblk) partials[(((long long)p * nblk + blk) * cp.np + q) * 6 + tid] = acc;
+            else atomicOr(status, ST_BOUNDS);
         }
         __syncthreads();
     }
@@ -840,6 +856,10 @@ __device__ __forceinline__ void refill_cell(const T* __restrict__ srcB, T* __res
         equilibrium((C)rbar, (C)v[0], (C)v[1], (C)v[2], k.rho0, fn);
     }
     collide_fluid(fn, k);
+    if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz) {
+        atomicOr(status, ST_BOUNDS);
+        return;
+    }
     store_own(dst, g, lin(g, x, y, z), fn);
 }
 

@@ -149,6 +149,7 @@ enum : int {
     ST_DOMAIN = 2,            // a particle left the domain through a closed wall
     ST_REFILL_SOLID = 4,      // refill found no particle owning a cell (internal)
     ST_UNSTABLE = 8,          // a particle state became non-finite or too fast
+    ST_BOUNDS = 16,           // an index check in a coupling kernel failed (access skipped)
 };
 
 // storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision), 4 = FP16
