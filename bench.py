@@ -42,6 +42,7 @@ K_BULK_F64_DP_INST_PER_CELL = 127.0
 K_BULK_F64_DRAM_BYTES_PER_CELL = 292.6
 FP64_LANE_OPS_PER_SM_CLK = 2
 COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI")
+FRAME_COUPLINGS = ("MEM_BB", "MEM_CLI", "MEM_MR", "PSM_M1B1", "PSM_M2B2")
 SHAPE = (128, 128, 512)
 WORKLOAD = ("settling sphere 128x128x512, D=24, rho_p/rho_f=1.5, Ga=144 (nu=0.01, tau=0.53), "
             "periodic x/y, no-slip z, released at rest 64 cells below the top; one global step "
@@ -253,7 +254,7 @@ def run_frame_study(args):
                 c, d, u = line.split()
                 table[(c, int(d))] = float(u)
     out = {}
-    for coupling in ("MEM_BB", "MEM_CLI", "PSM_M1B1", "PSM_M2B2"):
+    for coupling in args.frame_couplings:
         t0 = time.perf_counter()
         r = frame.run_frame(D=args.frame, coupling=coupling, storage="f64fx", stream=stream)
         paper = table.get((coupling, int(round(args.frame))))
@@ -612,7 +613,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--couplings", default=",".join(COUPLINGS))
+    ap.add_argument("--couplings", default=None,
+                    help="comma list; default PSM_M1B1,PSM_M2B2,MEM_BB,MEM_CLI (the settling "
+                         "step) or, with --frame, those and MEM_MR")
     ap.add_argument("--acc-steps", type=int, default=200)
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     ap.add_argument("--no-fp32", action="store_true")
@@ -627,7 +630,7 @@ def main():
     ap.add_argument("--learned-only", action="store_true")
     ap.add_argument("--frame", type=float, default=None, metavar="D",
                     help="run the paper's benchmark frame (case A, Ga = 144) at diameter D for "
-                         "MEM BB/CLI and PSM M1B1/M2B2 and print u_pV against the paper's Tab. 1")
+                         "MEM BB/CLI/MR and PSM M1B1/M2B2 and print u_pV against the paper's Tab. 1")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the settling workload by this factor in every length (tests)")
     ap.add_argument("--case-shape", default=None,
@@ -635,7 +638,12 @@ def main():
     ap.add_argument("--case-storage", default="f64",
                     choices=("f64", "f32", "f64ff", "f64fx", "f16s", "bf16s"))
     args = ap.parse_args()
-    args.couplings = tuple(c for c in args.couplings.split(",") if c)
+    args.frame_couplings = FRAME_COUPLINGS
+    if args.couplings is None:
+        args.couplings = COUPLINGS
+    else:
+        args.couplings = tuple(c for c in args.couplings.split(",") if c)
+        args.frame_couplings = args.couplings
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     if args.case_shape:

@@ -10,7 +10,9 @@
  *   - PSM, partially saturated cells (Sec. 2.3, Eq. (20)-(29), Algorithm 2),
  *     variants M1B1, M2B2, M3B2;
  *   - MEM, momentum exchange (Sec. 2.2, Eq. (12)-(19), Algorithm 1),
- *     boundary schemes BB and CLI (MR is reported as unsupported);
+ *     boundary schemes BB, CLI and MR (Eq. (12), (14), (15); the MR
+ *     coefficients, only cited by the paper, are derived for the TRT link
+ *     recurrence, see LBM_MEM_MR);
  * followed by the per-particle force/torque reduction and an explicit
  * rigid-body update of spherical particles.
  *
@@ -53,7 +55,7 @@ typedef enum {
                               /* cell or more per step (update not applied)       */
     LBM_ERR_DOMAIN = -5,      /* a particle left the domain through a closed wall */
     LBM_ERR_TIMEOUT = -6,     /* reserved: a bounded device wait gave up          */
-    LBM_ERR_UNSUPPORTED = -7  /* configuration not implemented (e.g. MEM MR)      */
+    LBM_ERR_UNSUPPORTED = -7  /* configuration not implemented (e.g. MR near |lambda_-| = 1) */
 } lbm_status;
 
 /* Coupling of Sec. 2.2 / 2.3.  LBM_NONE runs the plain fluid sweep. */
@@ -63,7 +65,19 @@ typedef enum {
     LBM_PSM_M3B2 = 2, /* Eq. (22) with Eq. (25)                      */
     LBM_MEM_BB = 3,   /* Eq. (12)                                    */
     LBM_MEM_CLI = 4,  /* Eq. (14)                                    */
-    LBM_MEM_MR = 5,   /* Eq. (15): coefficients not given; unsupported */
+    LBM_MEM_MR = 5,   /* Eq. (15) multi-reflection.  The paper cites its coefficients;
+                       * here they are derived from the second-order no-slip
+                       * requirement on the steady TRT link recurrence:
+                       * kappa_1 = 1, kappa_0 = (1-2d-2d^2)/(1+d)^2,
+                       * kappa_-1 = d^2/(1+d)^2, kappabar_-1 = -kappa_0,
+                       * kappabar_-2 = -kappa_-1, alpha = 4/(1+d)^2,
+                       * f^pc = -8 Lambda_- n^-_q(x,t) / ((2 Lambda_- + 1)(1+d)^2)
+                       * with d = delta_q and n^-_q the odd pre-collision
+                       * non-equilibrium at x, rebuilt from the stored
+                       * post-collision values.  Needs x - c_q and x - 2 c_q
+                       * fluid (else CLI, else BB).  Refused (LBM_ERR_UNSUPPORTED)
+                       * when |Lambda_- - 1/2| < 0.01, Lambda_- = Lambda/(tau-1/2)
+                       * (TRT) or tau - 1/2 (BGK), where the rebuild loses n^-. */
     LBM_NONE = 6
 } lbm_coupling;
 
@@ -144,7 +158,8 @@ enum {
 };
 
 /* Create a simulation.  Validates *cfg (LBM_ERR_ARG on a bad value,
- * LBM_ERR_UNSUPPORTED for LBM_MEM_MR), allocates two PDF buffers of
+ * LBM_ERR_UNSUPPORTED for LBM_MEM_MR with |Lambda_- - 1/2| < 0.01),
+ * allocates two PDF buffers of
  * 19*N elements on the current CUDA device and initialises the fluid at rest
  * (f = f_eq(rho0, 0), Eq. (3)).  stream: a cudaStream_t or NULL.
  * On success *out receives the handle; release it with lbm_destroy. */

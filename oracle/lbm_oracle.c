@@ -14,8 +14,8 @@
  *     with Eq. (20), (26), force/torque Eq. (28)-(29), stream Eq. (2), rigid
  *     body update.
  *   - MEM global step  = Algorithm 1 (Sec. 2.2): per LBM subcycle collide
- *     Eq. (1) with TRT Eq. (9), boundary conditions Eq. (12) / (14), stream
- *     Eq. (2), link forces Eq. (16); then average, total force/torque
+ *     Eq. (1) with TRT Eq. (9), boundary conditions Eq. (12) / (14) / (15),
+ *     stream Eq. (2), link forces Eq. (16); then average, total force/torque
  *     Eq. (17)-(18), rigid body update, re-mapping and PDF reconstruction
  *     Eq. (19).
  * The stored state between global steps is the pre-collision PDF field f
@@ -61,6 +61,24 @@
  *      the cell, a sample is inside iff |p - X_p| <= R (config: n = 4).
  * R16  Host-side particle replacement between steps (MEM): cells uncovered
  *      relative to the current mapping are set to f_eq(rho0, v).
+ * R17  MEM MR, Eq. (15): the paper takes kappa, alpha and f^pc from tables of
+ *      the cited TRT study, which are not at hand.  They are derived here
+ *      from the second-order no-slip requirement instead: along the link the
+ *      steady TRT recurrence (pre-collision non-equilibrium n^+- of the
+ *      equilibrium parts e^+-, Lambda_+- = 1/lambda_+- - 1/2 in magnitude) is
+ *      solved for equilibria quadratic in the link coordinate, and Eq. (15)
+ *      is required to return the population that would arrive from x + c_q
+ *      whenever u(x_b) = v(x_b), for any wall velocity, density, velocity
+ *      slope, velocity curvature and pressure gradient along the link.
+ *      With kappa_1 = 1, kappabar_-1 = -kappa_0 and kappabar_-2 = -kappa_-1
+ *      (the pairing of Eq. (14)) the solution is unique:
+ *        kappa_0 = (1 - 2 d - 2 d^2)/(1 + d)^2, kappa_-1 = d^2/(1 + d)^2,
+ *        alpha = 4/(1 + d)^2,
+ *        f^pc = -8 Lambda_- / ((2 Lambda_- + 1)(1 + d)^2) n^-_q(x, t),
+ *      d = delta_q, n^-_q = odd part of f_q - f_eq,q of the PRE-collision
+ *      populations at x (the stored old values of Sec. 4).  MR needs x - c_q
+ *      and x - 2 c_q to be fluid; where only x - c_q is, the link uses
+ *      Eq. (14) (CLI), else Eq. (12) with the BB weights (as R8).
  * R27  Open z boundaries of the benchmark frame (Sec. 4.1), bc_z = 2: at the
  *      bottom the velocity bounce-back of Eq. (12) with the inflow velocity
  *      u_in; at the top the outflow of Sec. 4.1, f_qbar(x,t+1) = -f~_q(x,t)
@@ -400,9 +418,29 @@ static double scheme_delta(const orc_sim *s, const orc_particle *P, const double
     return link_delta(s, P, x, q);
 }
 
+/* Eq. (15) with the coefficients of R17.  q is the link direction (towards
+ * the wall), qbar its opposite; ft_q0/1/2 = f~_q at x, x - c_q, x - 2 c_q;
+ * ft_qb0/1 = f~_qbar at x, x - c_q; n_minus = n^-_q(x, t) (R17); e_wall =
+ * w_q rho0 v(x_b) . c_q / c_s^2; Lambda_m = 1/|lambda_-| - 1/2. */
+double orc_mr_link(double delta, double Lambda_m, double ft_q0, double ft_q1, double ft_q2,
+                   double ft_qb0, double ft_qb1, double n_minus, double e_wall) {
+    double d1 = (1.0 + delta) * (1.0 + delta);
+    double kappa1 = 1.0;
+    double kappa0 = (1.0 - 2.0 * delta - 2.0 * delta * delta) / d1;
+    double kappam1 = delta * delta / d1;
+    double kappabm1 = -kappa0;
+    double kappabm2 = -kappam1;
+    double alpha = 4.0 / d1;
+    double kpc = -8.0 * Lambda_m / ((2.0 * Lambda_m + 1.0) * d1);
+    double fpc = kpc * n_minus;
+    return kappa1 * ft_q0 + kappa0 * ft_q1 + kappam1 * ft_q2 + kappabm1 * ft_qb0 +
+           kappabm2 * ft_qb1 - alpha * e_wall + fpc;
+}
+
 /* Boundary value f_qbar(x, t+1) for fluid x whose neighbour x + c_q is solid:
- * Eq. (12) BB or Eq. (14) CLI. */
-static double link_value(const orc_sim *s, int x, int y, int z, int q, const orc_particle *P) {
+ * Eq. (12) BB, Eq. (14) CLI or Eq. (15) MR.  fpre: pre-collision f(x, t). */
+static double link_value(const orc_sim *s, int x, int y, int z, int q, const orc_particle *P,
+                         const double fpre[NQ]) {
     long i = cell_index(s, x, y, z);
     int qb = OPP[q];
     double xc[3], xb[3], v[3];
@@ -412,22 +450,41 @@ static double link_value(const orc_sim *s, int x, int y, int z, int q, const orc
     body_velocity(s, P, xb, v);
     double vc = v[0] * CQ[q][0] + v[1] * CQ[q][1] + v[2] * CQ[q][2];
     double ftq = s->ft[(long)q * s->n + i];
-    if (s->p.coupling == ORC_MEM_CLI) {
+    double e_wall = (WQ[q] * INV_CS2) * s->p.rho0 * vc;
+    if (s->p.coupling == ORC_MEM_MR) {
+        long jb = neighbour(s, x, y, z, -CQ[q][0], -CQ[q][1], -CQ[q][2]);
+        long jb2 = neighbour(s, x, y, z, -2 * CQ[q][0], -2 * CQ[q][1], -2 * CQ[q][2]);
+        if (jb >= 0 && !s->solid[jb] && jb2 >= 0 && !s->solid[jb2]) {
+            /* n^-_q(x, t): odd part of the pre-collision non-equilibrium */
+            double rho, U[3];
+            moments(fpre, s->p.rho0, &rho, U);
+            double n_minus = 0.5 * (fpre[q] - fpre[qb]) -
+                             0.5 * (orc_feq(q, rho, U, s->p.rho0) - orc_feq(qb, rho, U, s->p.rho0));
+            double Lambda_m = -1.0 / s->lam_m - 0.5;
+            return orc_mr_link(delta, Lambda_m, ftq, s->ft[(long)q * s->n + jb],
+                               s->ft[(long)q * s->n + jb2], s->ft[(long)qb * s->n + i],
+                               s->ft[(long)qb * s->n + jb], n_minus, e_wall);
+        }
+        /* R17: x - 2 c_q missing, the CLI of Eq. (14) below (or BB) */
+    }
+    if (s->p.coupling == ORC_MEM_CLI || s->p.coupling == ORC_MEM_MR) {
         long jb = neighbour(s, x, y, z, -CQ[q][0], -CQ[q][1], -CQ[q][2]);
         if (jb >= 0 && !s->solid[jb]) {
             double kappa0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
             double alpha = 4.0 / (1.0 + 2.0 * delta);
             return ftq + kappa0 * s->ft[(long)q * s->n + jb] -
                    kappa0 * s->ft[(long)qb * s->n + i] -
-                   alpha * (WQ[q] * INV_CS2) * s->p.rho0 * vc;
+                   alpha * e_wall;
         }
         /* R8: second node missing, fall back to the BB weights */
     }
-    return ftq - 2.0 * (WQ[q] * INV_CS2) * s->p.rho0 * vc;
+    return ftq - 2.0 * e_wall;
 }
 
-/* "Apply boundary conditions", Algorithm 1: Eq. (12) / (14) on every
- * fluid-solid link.  Writes the post-stream value f_qbar(x, t+1). */
+/* "Apply boundary conditions", Algorithm 1: Eq. (12) / (14) / (15) on every
+ * fluid-solid link.  Writes the post-stream value f_qbar(x, t+1); the values
+ * of one cell are all computed before any is written, because MR reads the
+ * cell's pre-collision populations f(x, t). */
 static void mem_boundary(orc_sim *s) {
 #pragma omp parallel for
     for (int z = 0; z < s->p.nz; ++z)
@@ -435,12 +492,21 @@ static void mem_boundary(orc_sim *s) {
             for (int x = 0; x < s->p.nx; ++x) {
                 long i = cell_index(s, x, y, z);
                 if (s->solid[i]) continue;
+                double fpre[NQ], val[NQ];
+                int set[NQ];
+                for (int q = 0; q < NQ; ++q) {
+                    fpre[q] = s->f[(long)q * s->n + i];
+                    set[q] = 0;
+                }
                 for (int q = 1; q < NQ; ++q) {
                     long j = neighbour(s, x, y, z, CQ[q][0], CQ[q][1], CQ[q][2]);
                     if (j < 0 || !s->solid[j]) continue;
                     const orc_particle *P = &s->part[s->solid[j] - 1];
-                    s->f[(long)OPP[q] * s->n + i] = link_value(s, x, y, z, q, P);
+                    val[q] = link_value(s, x, y, z, q, P, fpre);
+                    set[q] = 1;
                 }
+                for (int q = 1; q < NQ; ++q)
+                    if (set[q]) s->f[(long)OPP[q] * s->n + i] = val[q];
             }
 }
 
@@ -831,7 +897,6 @@ void orc_get_macro(const orc_sim *s, double *rho_out, double *u_out) {
  * fluid step (no coupling). */
 static int one_step(orc_sim *s) {
     int c = s->p.coupling, np = s->np;
-    if (c == ORC_MEM_MR) return ORC_ERR_UNSUPPORTED;
     if (is_psm(c)) {
         for (int k = 0; k < 3 * np; ++k) { s->force[k] = 0.0; s->torque[k] = 0.0; }
         compute_solid_fractions(s);

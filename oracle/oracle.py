@@ -89,6 +89,8 @@ def _load():
         lib.orc_lattice.argtypes = [ct.POINTER(ct.c_int), dp, ct.POINTER(ct.c_int)]
         lib.orc_lambda_minus.restype = ct.c_double
         lib.orc_lambda_minus.argtypes = [P]
+        lib.orc_mr_link.restype = ct.c_double
+        lib.orc_mr_link.argtypes = [ct.c_double] * 9
         _lib = lib
         return lib
 
@@ -112,6 +114,13 @@ def feq(q: int, rho: float, U, rho0: float = 1.0) -> float:
     """Eq. (3) of the paper, evaluated by the oracle."""
     u = np.ascontiguousarray(U, dtype=np.float64)
     return _load().orc_feq(int(q), float(rho), _dp(u), float(rho0))
+
+
+def mr_link(delta, Lambda_m, ft_q0, ft_q1, ft_q2, ft_qb0, ft_qb1, n_minus, e_wall) -> float:
+    """Eq. (15) multi-reflection value f_qbar(x, t+1) of one link, with the
+    coefficients the oracle derives for it (reading R17 of the C file)."""
+    return _load().orc_mr_link(*(float(v) for v in (delta, Lambda_m, ft_q0, ft_q1, ft_q2,
+                                                       ft_qb0, ft_qb1, n_minus, e_wall)))
 
 
 class Oracle:

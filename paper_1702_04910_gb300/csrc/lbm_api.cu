@@ -144,6 +144,7 @@ Launch base_launch(lbm_handle* h) {
     L.cp.subsample = h->cfg.subsample;
     L.cp.tau = h->cfg.tau;
     L.cp.rho0 = h->cfg.rho0;
+    L.cp.mr_cpc = h->kind == 2 && h->variant == 2 ? mr_correction_scale(h->cfg) : 0.0;
     L.parts = h->d_parts;
     L.parts_prev = h->d_prev;
     L.partials = h->d_partials;
@@ -366,7 +367,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
           cfg->rho_out > 0.0 && std::isfinite(cfg->rho_out)))
         return LBM_ERR_ARG;
     if (cfg->subsample < 0 || cfg->subsample > 40 || cfg->lbm_subcycles < 0) return LBM_ERR_ARG;
-    if (cfg->coupling == LBM_MEM_MR) return LBM_ERR_UNSUPPORTED;
+    if (cfg->coupling == LBM_MEM_MR && !mr_supported(*cfg)) return LBM_ERR_UNSUPPORTED;
     if (cfg->collision == LBM_TRT) {
         double lp = -1.0 / cfg->tau;
         double denom = cfg->magic / (0.5 + 1.0 / lp) - 0.5;

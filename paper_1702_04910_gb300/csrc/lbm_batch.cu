@@ -268,12 +268,12 @@ lbm_status make_case(lbm_batch* b, int c, const lbm_config& cfg, const lbm_parti
     if (cfg.bc_z != 0 && cfg.bc_z != 1) return bad("bc_z must be 0 or 1");
     if (cfg.subsample < 0 || cfg.subsample > 40 || cfg.lbm_subcycles < 0 || cfg.lbm_subcycles > 16)
         return bad("subsample or subcycles out of range");
-    if (cfg.coupling == LBM_MEM_MR) {
-        std::snprintf(msg, sizeof(msg), "case %d: MEM MR is not supported", c);
+    if (cfg.coupling < LBM_PSM_M1B1 || cfg.coupling > LBM_MEM_MR)
+        return bad("coupling must be a PSM or MEM variant");
+    if (cfg.coupling == LBM_MEM_MR && !mr_supported(cfg)) {
+        std::snprintf(msg, sizeof(msg), "case %d: MEM MR needs |Lambda_- - 1/2| >= 0.01", c);
         return fail(b, LBM_ERR_UNSUPPORTED, msg);
     }
-    if (cfg.coupling < LBM_PSM_M1B1 || cfg.coupling > LBM_MEM_CLI)
-        return bad("coupling must be a PSM variant, MEM BB or MEM CLI");
     if (cfg.storage != storage) return bad("storage differs from case 0");
     double lp = -1.0 / cfg.tau, lm = lp;
     if (cfg.collision == LBM_TRT) {
@@ -313,6 +313,7 @@ lbm_status make_case(lbm_batch* b, int c, const lbm_config& cfg, const lbm_parti
     k.cp.subsample = cfg.subsample ? cfg.subsample : 4;
     k.cp.tau = cfg.tau;
     k.cp.rho0 = cfg.rho0;
+    k.cp.mr_cpc = cfg.coupling == LBM_MEM_MR ? mr_correction_scale(cfg) : 0.0;
     k.kd = make_coll<double>(lp, lm, cfg.rho0, cfg.force_density);
     k.kfx = make_coll<fx64>(lp, lm, cfg.rho0, cfg.force_density);
     region_extent(g, p.diameter, k.map_ext);

@@ -98,11 +98,12 @@ struct Coll {
 // Coupling constants (FP64: solid fractions, weights, forces).
 struct Coupl {
     int kind;         // 0 none, 1 PSM, 2 MEM
-    int variant;      // PSM: 0 M1B1, 1 M2B2, 2 M3B2; MEM: 0 BB, 1 CLI
+    int variant;      // PSM: 0 M1B1, 1 M2B2, 2 M3B2; MEM: 0 BB, 1 CLI, 2 MR
     int np;
     int subsample;
     double tau;
     double rho0;
+    double mr_cpc;    // MEM MR: -4 Lambda_- / (Lambda_- - 1/2), scale of the Eq. (15) correction
 };
 
 // ---------------------------------------------------------------------------

@@ -69,7 +69,11 @@ __device__ __forceinline__ void cross3(const double (&a)[3], const double (&b)[3
 
 // ---------------------------------------------------------------------------
 // MEM pull for a fluid cell: stream Eq. (2); links whose upstream cell is
-// solid take the boundary value Eq. (12) (BB) or Eq. (14) (CLI); resting
+// solid take the boundary value Eq. (12) (BB), Eq. (14) (CLI) or Eq. (15)
+// (MR, coefficients derived for the TRT link recurrence: kappa_1 = 1,
+// kappa_0 = (1 - 2d - 2d^2)/(1+d)^2, kappa_-1 = d^2/(1+d)^2, kappabar_-1 =
+// -kappa_0, kappabar_-2 = -kappa_-1, alpha = 4/(1+d)^2, d = delta_q; MR
+// falls back to CLI where x - 2 c_q is not fluid, CLI to BB); resting
 // closed walls take halfway bounce-back.  When `slots` is non-null the link
 // force Eq. (16) and its torque about X_p (arm x_b - X_p) are accumulated.
 //
@@ -83,12 +87,37 @@ __device__ __forceinline__ int owner_of(const Geom& g, const DevParticle* parts,
     return gm ? mapped_owner(g, parts, np, *gm, x, y, z) : cell_owner(g, parts, np, x, y, z);
 }
 
+// Post-collision momentum j~(x) of the boundary cell, loaded on the first MR
+// link of the cell (Eq. (15) correction term).
+struct MrCell {
+    double j[3];
+    bool have;
+};
+
+template <typename T>
+__device__ __forceinline__ void own_momentum(const T* __restrict__ src, const Geom& g,
+                                             long long idx, MrCell& mc) {
+    if (mc.have) return;
+    double j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+    for (int q = 1; q < NQ; ++q) {
+        const double v = ld_pdf(src + (long long)q * g.n + idx, q);
+        j0 += v * cx(q);
+        j1 += v * cy(q);
+        j2 += v * cz(q);
+    }
+    mc.j[0] = j0;
+    mc.j[1] = j1;
+    mc.j[2] = j2;
+    mc.have = true;
+}
+
 template <typename T, typename C, int Q>
 __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Geom& g,
                                              const Coupl& cp, const DevParticle* parts, int np,
                                              const GeoMap* gm, const Nbr& b, int x, int y, int z,
                                              long long idx, C (&f)[NQ], Slots* slots,
-                                             int* status) {
+                                             int* status, MrCell& mc) {
     constexpr int QP = opp(Q);  // paper's link direction (towards the solid cell)
     int xs, ys, zs;
     shifted<Q>(b, x, y, z, -1, xs, ys, zs);
@@ -124,18 +153,55 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
     const double wr = 3.0 * wq(QP) * cp.rho0;                 // w_q / c_s^2 * rho0
     double val;
     bool cli_done = false;
-    if (cp.variant == 1) {
-        // second node x - c_qp = x + c_q must be a fluid cell
+    if (cp.variant >= 1) {
+        // second node x - c_qp = x + c_q must be a fluid cell (CLI and MR)
         int x2, y2, z2;
         shifted<Q>(b, x, y, z, +1, x2, y2, z2);
         bool ok = !(cz(Q) != 0 && (z2 < 0 || z2 >= g.nz));
         if (ok) ok = owner_of(g, parts, np, gm, x2, y2, z2) == 0;
+        if (ok && (x2 < 0 || x2 >= g.nx || y2 < 0 || y2 >= g.ny || z2 < 0 || z2 >= g.nz)) {
+            atomicOr(status, ST_BOUNDS);
+            ok = false;
+        }
         if (ok) {
-            const double k0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
-            const double alpha = 4.0 / (1.0 + 2.0 * delta);
             const double f2 = ld_pdf(src + (long long)QP * g.n + lin(g, x2, y2, z2), QP);
             const double fq = ld_pdf(src + (long long)Q * g.n + idx, Q);
-            val = ftqp + k0 * f2 - k0 * fq - alpha * wr * vc;
+            bool mr_done = false;
+            if (cp.variant == 2) {
+                // Eq. (15): third node x - 2 c_qp = x + 2 c_q must be fluid too
+                int x3 = x2 + cx(Q), y3 = y2 + cy(Q), z3 = z2 + cz(Q);
+                x3 = x3 < 0 ? x3 + g.nx : (x3 >= g.nx ? x3 - g.nx : x3);
+                y3 = y3 < 0 ? y3 + g.ny : (y3 >= g.ny ? y3 - g.ny : y3);
+                bool ok3 = true;
+                if (g.bc_z) ok3 = z3 >= 0 && z3 < g.nz;
+                else z3 = z3 < 0 ? z3 + g.nz : (z3 >= g.nz ? z3 - g.nz : z3);
+                if (ok3) ok3 = owner_of(g, parts, np, gm, x3, y3, z3) == 0;
+                if (ok3 && (x3 < 0 || x3 >= g.nx || y3 < 0 || y3 >= g.ny || z3 < 0 || z3 >= g.nz)) {
+                    atomicOr(status, ST_BOUNDS);
+                    ok3 = false;
+                }
+                if (ok3) {
+                    const double f3 = ld_pdf(src + (long long)QP * g.n + lin(g, x3, y3, z3), QP);
+                    const double fq2 = ld_pdf(src + (long long)Q * g.n + lin(g, x2, y2, z2), Q);
+                    own_momentum(src, g, idx, mc);
+                    const double d1 = (1.0 + delta) * (1.0 + delta);
+                    const double k0 = (1.0 - 2.0 * delta - 2.0 * delta * delta) / d1;
+                    const double km1 = delta * delta / d1;
+                    const double alpha = 4.0 / d1;
+                    // (1 - |lambda_-|) n^-_qp(x, t), rebuilt from the stored values
+                    const double odd = 0.5 * (ftqp - fq) -
+                                       3.0 * wq(QP) *
+                                           (cx(QP) * mc.j[0] + cy(QP) * mc.j[1] + cz(QP) * mc.j[2]);
+                    val = ftqp + k0 * (f2 - fq) + km1 * (f3 - fq2) - alpha * wr * vc +
+                          cp.mr_cpc / d1 * odd;
+                    mr_done = true;
+                }
+            }
+            if (!mr_done) {
+                const double k0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
+                const double alpha = 4.0 / (1.0 + 2.0 * delta);
+                val = ftqp + k0 * f2 - k0 * fq - alpha * wr * vc;
+            }
             cli_done = true;
         }
     }
@@ -158,16 +224,18 @@ struct MemPull {
                                                const Coupl& cp, const DevParticle* parts, int np,
                                                const GeoMap* gm, const Nbr& b, int x, int y, int z,
                                                long long idx, C (&f)[NQ], Slots* slots,
-                                               int* status) {
-        mem_pull_one<T, C, Q>(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status);
-        MemPull<T, C, Q + 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status);
+                                               int* status, MrCell& mc) {
+        mem_pull_one<T, C, Q>(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status, mc);
+        MemPull<T, C, Q + 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status,
+                                  mc);
     }
 };
 template <typename T, typename C>
 struct MemPull<T, C, NQ> {
     __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const Coupl&,
                                                const DevParticle*, int, const GeoMap*, const Nbr&,
-                                               int, int, int, long long, C (&)[NQ], Slots*, int*) {}
+                                               int, int, int, long long, C (&)[NQ], Slots*, int*,
+                                               MrCell&) {}
 };
 
 template <typename T, typename C>
@@ -176,8 +244,10 @@ __device__ __forceinline__ void mem_pull(const T* __restrict__ src, const Geom& 
                                          int x, int y, int z, long long idx, C (&f)[NQ],
                                          Slots* slots, int* status) {
     Nbr b = make_nbr(g, x, y, z);
+    MrCell mc;
+    mc.have = false;
     f[0] = PdfStore<T>::template load<C>(src + idx, 0);
-    MemPull<T, C, 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status);
+    MemPull<T, C, 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status, mc);
 }
 
 // ---------------------------------------------------------------------------

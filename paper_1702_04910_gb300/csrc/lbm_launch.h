@@ -1,9 +1,10 @@
 // Host-side launch interface between the C-ABI layer and the kernels.
 // Internal to the library; not part of the public ABI.
 #pragma once
-
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 
 #include "../../include/lbm_gb300.h"
 #include "lbm_device.cuh"
@@ -103,6 +104,25 @@ struct BatchList {
 
 // Collision constants of Eq. (5) / (9)-(11) with the forcing of Eq. (7)
 // (computed in FP64, rounded once to C).
+// MEM MR, Eq. (15): Lambda_- = 1/|lambda_-| - 1/2 of the collision (TRT:
+// Lambda / (tau - 1/2), Eq. (11); BGK: tau - 1/2).  The correction term
+// f^pc = -8 Lambda_- n^-_q / ((2 Lambda_- + 1)(1 + delta)^2) needs the
+// pre-collision odd non-equilibrium n^-_q(x, t); the kernels rebuild it from
+// the stored post-collision values, (1 - |lambda_-|) n^-_q =
+// (f~_q - f~_qbar)/2 - 3 w_q c_q . j~ (the forcing drops out), so the scale
+// applied to that difference is -4 Lambda_- / (Lambda_- - 1/2).  The rebuild
+// loses n^- as |lambda_-| -> 1; MR is refused within 0.01 of Lambda_- = 1/2.
+inline double mr_lambda_minus(const lbm_config& cfg) {
+    return cfg.collision == LBM_TRT ? cfg.magic / (cfg.tau - 0.5) : cfg.tau - 0.5;
+}
+inline bool mr_supported(const lbm_config& cfg) {
+    return std::fabs(mr_lambda_minus(cfg) - 0.5) >= 0.01;
+}
+inline double mr_correction_scale(const lbm_config& cfg) {
+    const double Lm = mr_lambda_minus(cfg);
+    return -4.0 * Lm / (Lm - 0.5);
+}
+
 template <typename C>
 inline Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) {
     Coll<C> k{};

@@ -91,8 +91,8 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
         set_err(err, err_len, "lbm_sweep_noalloc takes FP64 PDF buffers only");
         return LBM_ERR_UNSUPPORTED;
     }
-    if (cfg->coupling == LBM_MEM_MR) {
-        set_err(err, err_len, "MEM MR is not supported");
+    if (cfg->coupling == LBM_MEM_MR && !mr_supported(*cfg)) {
+        set_err(err, err_len, "MEM MR needs |Lambda_- - 1/2| >= 0.01");
         return LBM_ERR_UNSUPPORTED;
     }
     const bool coupled = cfg->coupling != LBM_NONE;
@@ -194,6 +194,7 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     L.cp.subsample = cfg->subsample ? cfg->subsample : 4;
     L.cp.tau = cfg->tau;
     L.cp.rho0 = cfg->rho0;
+    L.cp.mr_cpc = L.cp.kind == 2 && L.cp.variant == 2 ? mr_correction_scale(*cfg) : 0.0;
     L.parts = a.particles;
     L.parts_prev = a.particles;
     L.partials = a.partials;

@@ -61,8 +61,11 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     cfg = binding.make_config((8, 8, 8), tau=0.4)  # tau <= 1/2 is invalid
     h = ct.c_void_p()
     assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_ARG
-    cfg = binding.make_config((8, 8, 8), coupling="MEM_MR")
-    assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_UNSUPPORTED
+    # MEM MR rebuilds its correction from post-collision values: refused where
+    # Lambda_- = 1/2 (TRT: Lambda / (tau - 1/2) with Lambda = 3/16; BGK: tau - 1/2)
+    for tau, coll in ((0.875, "TRT"), (0.88, "TRT"), (1.0, "BGK")):
+        cfg = binding.make_config((8, 8, 8), coupling="MEM_MR", tau=tau, collision=coll)
+        assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_UNSUPPORTED
     cfg = binding.make_config((0, 8, 8))
     assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_ARG
     lib.lbm_step.restype = ct.c_int
@@ -132,8 +135,8 @@ def test_batch_rejects_invalid_cases_without_gpu():
         return out
 
     parts = [c["particles"][0] for c in cases]
-    st, msg = create(cfgs_of(cases, coupling="MEM_MR"), parts)
-    assert st == binding.LBM_ERR_UNSUPPORTED and "case 0" in msg
+    st, msg = create(cfgs_of(cases, coupling="MEM_MR", tau=0.875), parts)  # Lambda_- = 1/2
+    assert st == binding.LBM_ERR_UNSUPPORTED and "case 0" in msg and "MR" in msg
     st, msg = create(cfgs_of(cases, coupling="NONE"), parts)
     assert st == binding.LBM_ERR_ARG
     cfgs = cfgs_of(cases)

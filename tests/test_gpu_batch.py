@@ -17,15 +17,16 @@ pytestmark = pytest.mark.gpu
 
 PDF_TOL = 1e-12
 FORCE_TOL = 1e-10
-MEM = ("MEM_BB", "MEM_CLI")
+MEM = ("MEM_BB", "MEM_CLI", "MEM_MR")
 
 
 def small_ensemble(seed=3):
-    """Five uneven cases (D = 5..7) covering every coupling the batch takes.
+    """Six uneven cases (D = 5..7) covering every coupling the batch takes.
     PSM M3B2 is held fixed (a free sphere of density ratio 1.5 grows unstable
     under it) in a flow driven by a lateral body force."""
-    cases = W.ensemble(5, seed=seed, d_range=(5, 7),
-                       couplings=("PSM_M1B1", "MEM_BB", "PSM_M2B2", "MEM_CLI", "PSM_M3B2"))
+    cases = W.ensemble(6, seed=seed, d_range=(5, 7),
+                       couplings=("PSM_M1B1", "MEM_BB", "PSM_M2B2", "MEM_CLI", "PSM_M3B2",
+                                  "MEM_MR"))
     cases[4]["particles"][0]["fixed"] = 1
     cases[4]["fext"] = (2e-5, 0.0, 0.0)
     return cases
@@ -88,7 +89,7 @@ def test_batch_tilings_and_autotune_are_bitwise_neutral():
     from paper_1702_04910_gb300.binding import Batch
     cases = small_ensemble(seed=11)
     ref = None
-    mixed = ["box64", "plane", "box32", "box128", "plane"]
+    mixed = ["box64", "plane", "box32", "box128", "plane", "box32"]
     for layout, grid in (("plane", 0), ("box32", 0), ("box64", 152), ("box128", 1), ("plane", 7),
                          (mixed, 300)):
         b = Batch(cases)

@@ -29,7 +29,7 @@ def table1():
     return out
 
 
-@pytest.mark.parametrize("coupling", ["MEM_BB", "MEM_CLI", "PSM_M1B1", "PSM_M2B2"])
+@pytest.mark.parametrize("coupling", ["MEM_BB", "MEM_CLI", "MEM_MR", "PSM_M1B1", "PSM_M2B2"])
 def test_frame_case_a_matches_table_1(coupling):
     from paper_1702_04910_gb300 import frame
     res = frame.run_frame(D=18.0, ga_target=144.0, coupling=coupling, storage="f64fx")

@@ -118,13 +118,14 @@ def moving_sphere_case(coupling, D=9.0, shape=(40, 36, 48), collision="TRT", fre
 # reflect the relative momentum, j' - rho0 v = -(j - rho0 v), and the coupled
 # interior mode grows by 1 + 2 rho_f / rho_p per step for a free sphere.
 MOVING = [("PSM_M1B1", True), ("PSM_M2B2", True), ("PSM_M3B2", False), ("MEM_BB", True),
-          ("MEM_CLI", True), ("MEM_CLI", False)]
+          ("MEM_CLI", True), ("MEM_CLI", False), ("MEM_MR", True), ("MEM_MR", False)]
 
 
 @pytest.mark.parametrize("coupling,free,storage",
                          [m + ("f64",) for m in MOVING] +
                          [("PSM_M2B2", True, "f64ff"), ("MEM_CLI", True, "f64ff"),
-                          ("PSM_M2B2", True, "f64fx"), ("MEM_CLI", True, "f64fx")])
+                          ("PSM_M2B2", True, "f64fx"), ("MEM_CLI", True, "f64fx"),
+                          ("MEM_MR", True, "f64fx")])
 def test_moving_sphere_parity(lattice, coupling, free, storage):
     case = moving_sphere_case(coupling, free=free)
     o, g = make_pair(case, storage=storage)
@@ -151,7 +152,7 @@ def test_moving_sphere_parity(lattice, coupling, free, storage):
     assert np.max(np.abs(u_g - u_o)) < 1e-12
 
 
-@pytest.mark.parametrize("coupling", ["PSM_M1B1", "MEM_CLI"])
+@pytest.mark.parametrize("coupling", ["PSM_M1B1", "MEM_CLI", "MEM_MR"])
 def test_two_spheres_parity(lattice, coupling):
     case = moving_sphere_case(coupling, shape=(48, 40, 40))
     p0 = dict(case["particles"][0])
@@ -170,7 +171,7 @@ def test_two_spheres_parity(lattice, coupling):
 
 
 @pytest.mark.parametrize("coupling,free", [("PSM_M2B2", True), ("PSM_M3B2", False),
-                                          ("MEM_BB", True)])
+                                          ("MEM_BB", True), ("MEM_MR", True)])
 def test_periodic_wrap_of_a_sphere(lattice, coupling, free):
     """A sphere straddling the periodic x and y faces (minimum image)."""
     case = moving_sphere_case(coupling, shape=(32, 34, 30), free=free)
@@ -200,9 +201,49 @@ def test_fixed_sphere_box_1000_steps(lattice, coupling, storage):
     compare_forces(o, g)
 
 
+# ---- MEM MR, Eq. (15): relaxation times near the rebuild limit, links that fall back ------
+@pytest.mark.parametrize("tau", [0.53, 0.9, 1.6])
+def test_mr_fixed_sphere_parity(lattice, tau):
+    """MR on the fixed-sphere box under a body force: the correction term's
+    odd non-equilibrium is taken from the pre-collision values by the oracle
+    and rebuilt from the stored post-collision values (scaled by
+    1/(1 - |lambda_-|), up to 31 at tau = 0.9) by the kernels."""
+    case = W.fixed_sphere_box(L=32, D=8.0, tau=tau, force=4.4e-6, coupling="MEM_MR",
+                              collision="TRT")
+    o, g = make_pair(case)
+    start(o, g, lattice)
+    o.step(200)
+    g.step(200)
+    compare_pdf(o, g)
+    compare_forces(o, g)
+
+
+def test_mr_links_fall_back_near_a_wall_and_a_neighbour(lattice):
+    """Two spheres 1.6 cells apart, the lower one 1.3 cells above a closed
+    wall: links whose x - 2 c_q (or x - c_q) is solid or beyond the wall take
+    the CLI (or BB) value, on both sides."""
+    case = moving_sphere_case("MEM_MR", shape=(40, 36, 44))
+    p0 = dict(case["particles"][0])
+    p0["x"] = (19.7, 18.2, 1.3 + 0.5 * p0["diameter"])
+    p0["u"] = (0.01, -0.02, 0.0)
+    p1 = dict(p0)
+    p1["x"] = (19.1, 18.6, p0["x"][2] + p0["diameter"] + 1.6)
+    p1["u"] = (-0.01, 0.02, -0.01)
+    case["particles"] = [p0, p1]
+    case["bc_z"] = 1
+    o, g = make_pair(case)
+    start(o, g, lattice, amp=0.02, seed=4)
+    o.step(12)
+    g.step(12)
+    compare_pdf(o, g)
+    compare_forces(o, g)
+    compare_particles(o, g)
+
+
 # ---- the 128 x 128 x 512 settling workload at full size, as the benchmark runs it --------
 @pytest.mark.parametrize("coupling,storage", [("MEM_CLI", "f64"), ("PSM_M2B2", "f64"),
-                                              ("PSM_M3B2", "f64"), ("MEM_CLI", "f64ff"),
+                                              ("PSM_M3B2", "f64"), ("MEM_MR", "f64"),
+                                              ("MEM_CLI", "f64ff"),
                                               ("PSM_M2B2", "f64ff"), ("MEM_CLI", "f64fx"),
                                               ("PSM_M2B2", "f64fx")])
 def test_settling_full_size_parity(lattice, coupling, storage):
@@ -239,7 +280,7 @@ def test_checkpoint_restart_is_bitwise(lattice, coupling):
 
 
 # ---- FP32 storage and arithmetic ------------------------------------------------------------
-@pytest.mark.parametrize("coupling", ["PSM_M2B2", "MEM_CLI"])
+@pytest.mark.parametrize("coupling", ["PSM_M2B2", "MEM_CLI", "MEM_MR"])
 def test_fp32_storage_tracks_fp64(lattice, coupling):
     """FP32 PDFs with FP32 collision against the FP64 oracle.  Each sweep adds
     a relative rounding error of order 2^-24 ~ 6e-8 per population; over 25
@@ -263,6 +304,7 @@ def test_fp32_storage_tracks_fp64(lattice, coupling):
 # populations, follow at the same relative order (1e-2 / 5e-2 bars).
 @pytest.mark.parametrize("coupling,storage,pdf_tol,force_tol",
                          [("PSM_M2B2", "f16s", 2e-4, 1e-2), ("MEM_CLI", "f16s", 2e-4, 1e-2),
+                          ("MEM_MR", "f16s", 2e-4, 1e-2),
                           ("PSM_M2B2", "bf16s", 2e-3, 5e-2), ("MEM_CLI", "bf16s", 2e-3, 5e-2)])
 def test_shifted_16bit_storage_tracks_fp64(lattice, coupling, storage, pdf_tol, force_tol):
     case = moving_sphere_case(coupling)
@@ -316,7 +358,8 @@ def test_open_boundaries_parity(lattice, storage):
 
 
 @pytest.mark.parametrize("coupling,collision", [("PSM_M2B2", "BGK"), ("PSM_M1B1", "BGK"),
-                                                ("MEM_CLI", "TRT"), ("MEM_BB", "TRT")])
+                                                ("MEM_CLI", "TRT"), ("MEM_BB", "TRT"),
+                                                ("MEM_MR", "TRT")])
 def test_frame_fixed_sphere_parity(lattice, coupling, collision):
     """A fixed sphere in the inflow/outflow frame (5.34D x 5.34D x 16D at D = 6)."""
     case = {"shape": (32, 32, 96), "bc_z": 2, "coupling": coupling, "collision": collision,

@@ -8,12 +8,14 @@ swapped index, a transposed operand) breaks at least one of them.
 """
 import numpy as np
 import pytest
+import scipy.sparse
+import scipy.sparse.linalg
 
 from oracle import oracle as orc
 from oracle.oracle import Oracle
 from paper_1702_04910_gb300 import workloads as W
 
-ALL_COUPLED = ["PSM_M1B1", "PSM_M2B2", "PSM_M3B2", "MEM_BB", "MEM_CLI"]
+ALL_COUPLED = ["PSM_M1B1", "PSM_M2B2", "PSM_M3B2", "MEM_BB", "MEM_CLI", "MEM_MR"]
 
 
 def moments(f, c):
@@ -215,10 +217,11 @@ def test_uniform_translation_is_force_free(lattice, coupling):
     subtracted, Sec. 2.3 solid operators): a sphere moving with the uniform
     fluid velocity V leaves f = f_eq(rho0, V) unchanged and feels no force.
     The CLI check holds for every delta only with the printed kappa_0 and alpha.
-    The torque vanishes too, except for CLI: there the Galilean term
+    The torque vanishes too, except for CLI and MR: there the Galilean term
     -v (f~_q - f_qbar) acts at x_b = x + delta_q c_q, and the discrete chord
     sums differ between lattice directions, so a small torque V x (...) remains
-    (an exact property of Eq. (16)-(18) with CLI, not round-off)."""
+    (an exact property of Eq. (16)-(18) with CLI, not round-off).  For MR the
+    check holds only with alpha = 2 (kappa_1 + kappa_0 + kappa_-1)."""
     c, w, _ = lattice
     V = np.array([0.03, -0.02, 0.015])
     shape = (20, 20, 20)
@@ -230,7 +233,7 @@ def test_uniform_translation_is_force_free(lattice, coupling):
         o.step(1)
         F, T = o.forces()
         assert np.max(np.abs(F)) < 1e-13
-        if coupling != "MEM_CLI":
+        if coupling not in ("MEM_CLI", "MEM_MR"):
             assert np.max(np.abs(T)) < 1e-12
     f = o.pdf("pre")
     fluid = (o.solid() == 0)
@@ -262,7 +265,7 @@ def test_psm_momentum_balance(lattice, coupling):
     assert np.max(np.abs(F)) > 1e-4  # the exchange is not trivially zero
 
 
-@pytest.mark.parametrize("coupling", ["MEM_BB", "MEM_CLI"])
+@pytest.mark.parametrize("coupling", ["MEM_BB", "MEM_CLI", "MEM_MR"])
 @pytest.mark.parametrize("subcycles", [1, 2])
 def test_mem_momentum_balance(lattice, coupling, subcycles):
     """For a resting sphere the link force Eq. (16) is exactly the momentum
@@ -336,6 +339,68 @@ def test_refilled_cells_carry_body_velocity(lattice):
             assert 0.5 < rho[z, y, x] < 1.5
             seen += 1
     assert seen > 10
+
+
+# ---- MEM MR, Eq. (15): second-order exactness on one link ---------------------------------
+def _steady_link(N, lam_p, lam_m, e_plus, e_minus):
+    """Brute-force steady state of one TRT link: populations q (along +s) and
+    qbar (along -s) on nodes s = -N..N with PRESCRIBED equilibrium parts
+    e_plus(s), e_minus(s); equilibrium enters at both ends.  Solves the linear
+    system  f_q(s) = f~_q(s-1),  f_qbar(s) = f~_qbar(s+1)  directly.
+    Returns s, pre-collision f_q, f_qbar and post-collision f~_q, f~_qbar."""
+    s = np.arange(-N, N + 1)
+    M = s.size
+    Ep, Em = e_plus(s), e_minus(s)
+    # f~_q = f_q - lam_p (f+ - e+) - lam_m (f- - e-), f~_qbar with -f-, -e-
+    aq, bq, cq = 1 - lam_p / 2 - lam_m / 2, -lam_p / 2 + lam_m / 2, lam_p * Ep + lam_m * Em
+    ab, bb, cb = -lam_p / 2 + lam_m / 2, 1 - lam_p / 2 - lam_m / 2, lam_p * Ep - lam_m * Em
+    A = scipy.sparse.lil_matrix((2 * M, 2 * M))
+    A.setdiag(1.0)
+    r = np.zeros(2 * M)
+    r[0], r[2 * M - 1] = Ep[0] + Em[0], Ep[-1] - Em[-1]
+    for k in range(1, M):
+        A[k, k - 1] -= aq
+        A[k, M + k - 1] -= bq
+        r[k] = cq[k - 1]
+    for k in range(M - 1):
+        A[M + k, k + 1] -= ab
+        A[M + k, M + k + 1] -= bb
+        r[M + k] = cb[k + 1]
+    x = scipy.sparse.linalg.spsolve(A.tocsr(), r)
+    fq, fb = x[:M], x[M:]
+    return s, fq, fb, aq * fq + bq * fb + cq, ab * fq + bb * fb + cb
+
+
+@pytest.mark.parametrize("delta", [0.02, 0.3, 0.5, 0.77, 1.0])
+@pytest.mark.parametrize("Lambda_p", [0.03, 0.3, 1.5])
+@pytest.mark.parametrize("magic", [True, False])
+def test_mr_closure_is_exact_for_parabolic_links(delta, Lambda_p, magic):
+    """The MR value of Eq. (15) returns the population that the continued
+    lattice would send from x + c_q, for any wall position delta, relaxation
+    pair and equilibrium with a wall velocity, a velocity slope and curvature
+    and a pressure (e+) gradient along the link: the second-order no-slip
+    property the multi-reflection scheme is built for.  The reference is a
+    direct linear solve of the lattice recurrence, not the closure's formula;
+    dropping f^pc, taking its non-equilibrium after collision, or any wrong
+    kappa leaves errors of order 1e-3 here."""
+    Lambda_m = 3.0 / 16.0 / Lambda_p if magic else Lambda_p
+    lam_p, lam_m = 1.0 / (Lambda_p + 0.5), 1.0 / (Lambda_m + 0.5)
+    rng = np.random.default_rng(int(100 * delta) + int(100 * Lambda_p) + magic)
+    a0, a1, a2, b1 = rng.normal(size=4) * [0.01, 0.003, 0.001, 0.002]
+    b0 = 1.0 / 18.0
+    e_minus = lambda s: a0 + a1 * (s - delta) + 0.5 * a2 * (s - delta) ** 2
+    e_plus = lambda s: b0 + b1 * (s - delta)
+    N = 400
+    s, fq, fb, ftq, ftb = _steady_link(N, lam_p, lam_m, e_plus, e_minus)
+    i = N  # the boundary node x at s = 0; the wall at s = delta
+    n_minus = 0.5 * (fq[i] - fb[i]) - e_minus(0.0)
+    got = orc.mr_link(delta, Lambda_m, ftq[i], ftq[i - 1], ftq[i - 2], ftb[i], ftb[i - 1],
+                      n_minus, a0)
+    assert abs(got - ftb[i + 1]) < 1e-14
+    # the same link without the correction term is wrong at second order
+    plain = orc.mr_link(delta, Lambda_m, ftq[i], ftq[i - 1], ftq[i - 2], ftb[i], ftb[i - 1],
+                        0.0, a0)
+    assert abs(plain - ftb[i + 1]) > 1e-6
 
 
 # ---- Fig. 1: drag on a simple-cubic sphere array in Stokes flow ------------------------------
