@@ -4,7 +4,7 @@ workload (D = 24, density ratio 1.5, Galileo number 144, closed top and bottom).
 
 One benchmark step is one global time step of each coupling variant that
 stays stable for a freely settling sphere (PSM M1B1, M2B2: one LBM sweep each;
-MEM BB, CLI: two LBM sweeps each, with refilling), each in its own simulation,
+MEM BB, CLI, MR: two LBM sweeps each, with refilling), each in its own simulation,
 FP64 PDFs and arithmetic.  MLUPS counts every lattice cell of every sweep.
 (PSM M3B2 runs the same kernel; as printed, with an explicit rigid-body
 update, it diverges for a free sphere, so it is not part of the timed step.)
@@ -41,12 +41,12 @@ METRIC = "MLUPS and % of HBM roofline, coupled D3Q19 step; force/velocity error 
 K_BULK_F64_DP_INST_PER_CELL = 127.0
 K_BULK_F64_DRAM_BYTES_PER_CELL = 292.6
 FP64_LANE_OPS_PER_SM_CLK = 2
-COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI")
+COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI", "MEM_MR")
 FRAME_COUPLINGS = ("MEM_BB", "MEM_CLI", "MEM_MR", "PSM_M1B1", "PSM_M2B2")
 SHAPE = (128, 128, 512)
 WORKLOAD = ("settling sphere 128x128x512, D=24, rho_p/rho_f=1.5, Ga=144 (nu=0.01, tau=0.53), "
             "periodic x/y, no-slip z, released at rest 64 cells below the top; one global step "
-            "of each of PSM M1B1/M2B2 (1 sweep) and MEM BB/CLI (2 sweeps, refilling)")
+            "of each of PSM M1B1/M2B2 (1 sweep) and MEM BB/CLI/MR (2 sweeps, refilling)")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -197,7 +197,7 @@ def run_ensemble(args, stream, world, dist, barrier, peak, storages=("f64", "f64
             "ms_per_step": ms / args.steps, "steps": args.steps, "cases": len(cases),
             "cells": cells, "cell_updates_per_step": cu,
             "workload": "seeded ensemble: D ~ U{8..20}, domain round(5.3D)^2 x round(16D), "
-                        "Ga ~ U(100, 250), density ratio 1.5, PSM M1B1/M2B2 and MEM BB/CLI",
+                        "Ga ~ U(100, 250), density ratio 1.5, PSM M1B1/M2B2 and MEM BB/CLI/MR",
             "tuning": {"layouts": {k: layouts.count(k) for k in sorted(set(layouts))},
                        "grid_blocks": grid, "bulk_ms": tune_ms},
             "bulk_GBps": bulk_gbps, "frac": bulk_gbps / peak,
@@ -529,7 +529,7 @@ def build_oracles(scale: float = 1.0):
 
 def cpu_baseline(steps: int, scale: float = 1.0):
     """The FP64 oracle (as it stands) on the same workload: `steps` global steps
-    of the four variants on the full domain, host cores."""
+    of the five variants on the full domain, host cores."""
     sims = build_oracles(scale)
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -542,7 +542,7 @@ def cpu_baseline(steps: int, scale: float = 1.0):
         o.close()
     return {"value": ncell * sweeps * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle_threads(),
             "kind": "oracle",
-            "sample": f"{steps} global step(s) of the four variants on the full 128x128x512 domain "
+            "sample": f"{steps} global step(s) of the five variants on the full 128x128x512 domain "
                       f"({steps * sweeps} sweeps, {dt:.1f} s)"}
 
 
@@ -563,7 +563,7 @@ def run_reference(args):
     ncell = shape[0] * shape[1] * shape[2]
     value = ncell * sweeps * args.steps / dt / 1e6
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    sample = (f"each step: one global step of the four variants on the full 128x128x512 domain "
+    sample = (f"each step: one global step of the five variants on the full 128x128x512 domain "
               f"({sweeps} sweeps)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -614,8 +614,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--couplings", default=None,
-                    help="comma list; default PSM_M1B1,PSM_M2B2,MEM_BB,MEM_CLI (the settling "
-                         "step) or, with --frame, those and MEM_MR")
+                    help="comma list; default PSM_M1B1,PSM_M2B2,MEM_BB,MEM_CLI,MEM_MR (the "
+                         "settling step; the same five with --frame)")
     ap.add_argument("--acc-steps", type=int, default=200)
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     ap.add_argument("--no-fp32", action="store_true")

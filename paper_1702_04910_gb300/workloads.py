@@ -99,7 +99,7 @@ def sim_kwargs(case: dict) -> dict:
     return kw
 
 
-ENSEMBLE_COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI")
+ENSEMBLE_COUPLINGS = ("PSM_M1B1", "PSM_M2B2", "MEM_BB", "MEM_CLI", "MEM_MR")
 
 
 def ensemble(n_cases: int = 64, seed: int = 0, d_range=(8, 20), ga_range=(100.0, 250.0),

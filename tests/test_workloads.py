@@ -21,7 +21,8 @@ def test_ensemble_follows_its_recipe():
         assert abs(x[2] - (c["shape"][2] - 8 * D / 3)) < 1e-9
         assert c["particles"][0]["density"] == 1.5
     counts = {k: sum(c["coupling"] == k for c in cases) for k in W.ENSEMBLE_COUPLINGS}
-    assert all(v == 16 for v in counts.values())
+    assert sum(counts.values()) == len(cases)  # round robin over the couplings
+    assert max(counts.values()) - min(counts.values()) <= 1
 
 
 def Ga_of(case, nu):

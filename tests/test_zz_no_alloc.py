@@ -31,7 +31,7 @@ def _case(coupling):
     return case
 
 
-@pytest.mark.parametrize("coupling", ["PSM_M2B2", "MEM_CLI"])
+@pytest.mark.parametrize("coupling", ["PSM_M2B2", "MEM_CLI", "MEM_MR"])
 def test_noalloc_sweep_matches_handle_step(lattice, coupling):
     import torch
 
