@@ -502,6 +502,21 @@ __global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
 // force/torque sums land in partials[((p * nblk + blk) * np + q) * 6 + c].
 // `sp` holds the particle records in shared memory; every thread of the
 // block must call this (it synchronises for the reduction).
+// MEM: a cell whose centre lies farther than R + 3/2 from every sphere centre
+// has no solid neighbour (neighbour centres are at most sqrt(2) away and a
+// cell is solid iff its centre is within R, R6), so its pull is the plain one.
+__device__ __forceinline__ bool clear_of_particles(const Geom& g, const DevParticle* sp, int np,
+                                                   int x, int y, int z) {
+    const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
+    for (int s = 0; s < np; ++s) {
+        double dx, dy, dz;
+        separation(g, xc, yc, zc, sp[s], dx, dy, dz);
+        const double r = sp[s].r + 1.5;
+        if (dx * dx + dy * dy + dz * dz <= r * r) return false;
+    }
+    return true;
+}
+
 template <typename T, typename C, int KIND, bool NOSTREAM>
 __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restrict__ dst,
                                            const Geom& g, const Coll<C>& k, const Coupl& cp,
@@ -537,6 +552,8 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
             if (!own) {
                 if (NOSTREAM)
                     load_own(src, g, idx, f);
+                else if (clear_of_particles(g, sp, cp.np, x, y, z))
+                    pull_plain(src, g, x, y, z, idx, f);  // no solid neighbour, no link
                 else
                     mem_pull(src, g, cp, sp, cp.np, &gm, x, y, z, idx, f, &slots, status);
                 collide_fluid(f, k);
