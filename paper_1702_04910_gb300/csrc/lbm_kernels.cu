@@ -112,13 +112,37 @@ __device__ __forceinline__ void own_momentum(const T* __restrict__ src, const Ge
     mc.have = true;
 }
 
+// Lattice velocities for a direction known only at run time (the link loop):
+// two bits per direction holding c + 1.
+template <int A>
+__host__ __device__ constexpr unsigned long long c_bits() {
+    unsigned long long b = 0;
+    for (int q = 0; q < NQ; ++q)
+        b |= (unsigned long long)((A == 0 ? cx(q) : (A == 1 ? cy(q) : cz(q))) + 1) << (2 * q);
+    return b;
+}
+__device__ __forceinline__ int rcx(int q) { return (int)((c_bits<0>() >> (2 * q)) & 3ull) - 1; }
+__device__ __forceinline__ int rcy(int q) { return (int)((c_bits<1>() >> (2 * q)) & 3ull) - 1; }
+__device__ __forceinline__ int rcz(int q) { return (int)((c_bits<2>() >> (2 * q)) & 3ull) - 1; }
+
+// Coordinates of x + sign * c_q (sign = +1 or -1), q known at run time.
+__device__ __forceinline__ void shifted_rt(const Nbr& b, int x, int y, int z, int q, int sign,
+                                           int& xs, int& ys, int& zs) {
+    const int dx = sign * rcx(q), dy = sign * rcy(q), dz = sign * rcz(q);
+    xs = dx > 0 ? b.xp : (dx < 0 ? b.xm : x);
+    ys = dy > 0 ? b.yp : (dy < 0 ? b.ym : y);
+    zs = dz > 0 ? b.zp : (dz < 0 ? b.zm : z);
+}
+
+// Phase 1 of the MEM pull, one direction Q: resting wall -> halfway
+// bounce-back; fluid upstream cell -> stream Eq. (2); solid upstream cell ->
+// bit Q of `cut`, filled by the link loop.
 template <typename T, typename C, int Q>
 __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Geom& g,
-                                             const Coupl& cp, const DevParticle* parts, int np,
-                                             const GeoMap* gm, const Nbr& b, int x, int y, int z,
-                                             long long idx, C (&f)[NQ], Slots* slots,
-                                             int* status, MrCell& mc) {
-    constexpr int QP = opp(Q);  // paper's link direction (towards the solid cell)
+                                             const DevParticle* parts, int np, const GeoMap* gm,
+                                             const Nbr& b, int x, int y, int z, long long idx,
+                                             C (&f)[NQ], unsigned& cut, int* status) {
+    constexpr int QP = opp(Q);
     int xs, ys, zs;
     shifted<Q>(b, x, y, z, -1, xs, ys, zs);
     if (cz(Q) != 0 && (zs < 0 || zs >= g.nz)) {
@@ -141,35 +165,76 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
         f[Q] = (C)0.0;
         return;
     }
+    cut |= 1u << Q;
+}
+
+template <typename T, typename C, int Q>
+struct MemPull {
+    __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
+                                               const DevParticle* parts, int np, const GeoMap* gm,
+                                               const Nbr& b, int x, int y, int z, long long idx,
+                                               C (&f)[NQ], unsigned& cut, int* status) {
+        mem_pull_one<T, C, Q>(src, g, parts, np, gm, b, x, y, z, idx, f, cut, status);
+        MemPull<T, C, Q + 1>::run(src, g, parts, np, gm, b, x, y, z, idx, f, cut, status);
+    }
+};
+template <typename T, typename C>
+struct MemPull<T, C, NQ> {
+    __device__ __forceinline__ static void run(const T* __restrict__, const Geom&,
+                                               const DevParticle*, int, const GeoMap*, const Nbr&,
+                                               int, int, int, long long, C (&)[NQ], unsigned&,
+                                               int*) {}
+};
+
+// Phase 2: the boundary value f_q(x, t+1) of one cut link (q filled at x,
+// qp = qbar the paper's link direction towards the solid cell x + c_qp):
+// Eq. (12) BB, Eq. (14) CLI or Eq. (15) MR, and, when `ft` is non-null, the
+// link force Eq. (16) and its torque about X_p (arm x_b - X_p) in ft[0..5],
+// with the owning particle's 1-based index in *owner_out (0: no force).
+template <typename T>
+__device__ __forceinline__ double mem_link(const T* __restrict__ src, const Geom& g, const Coupl& cp,
+                                        const DevParticle* parts, int np, const GeoMap* gm,
+                                        const Nbr& b, int x, int y, int z, long long idx, int q,
+                                        double* ft, int* owner_out, int* status, MrCell& mc) {
+    if (ft) *owner_out = 0;
+    const int qp = opp(q);
+    const double cqx = rcx(qp), cqy = rcy(qp), cqz = rcz(qp);  // c_qp
+    int xs, ys, zs;
+    shifted_rt(b, x, y, z, q, -1, xs, ys, zs);  // x - c_q = x + c_qp, solid
+    const int owner = owner_of(g, parts, np, gm, xs, ys, zs);
+    if (owner < 1 || owner > np) {
+        atomicOr(status, ST_BOUNDS);
+        return 0.0;
+    }
     const DevParticle& P = parts[owner - 1];
     const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
     const double delta =
-        cp.variant == 0 ? 0.5 : link_delta(g, P, xc, yc, zc, cx(QP), cy(QP), cz(QP));
-    const double xb[3] = {xc + delta * cx(QP), yc + delta * cy(QP), zc + delta * cz(QP)};
+        cp.variant == 0 ? 0.5 : link_delta(g, P, xc, yc, zc, rcx(qp), rcy(qp), rcz(qp));
+    const double xb[3] = {xc + delta * cqx, yc + delta * cqy, zc + delta * cqz};
     double v[3];
     body_velocity(g, P, xb[0], xb[1], xb[2], v[0], v[1], v[2]);
-    const double vc = v[0] * cx(QP) + v[1] * cy(QP) + v[2] * cz(QP);
-    const double ftqp = ld_pdf(src + (long long)QP * g.n + idx, QP);  // f~_qp(x)
-    const double wr = 3.0 * wq(QP) * cp.rho0;                 // w_q / c_s^2 * rho0
+    const double vc = v[0] * cqx + v[1] * cqy + v[2] * cqz;
+    const double ftqp = ld_pdf(src + (long long)qp * g.n + idx, qp);  // f~_qp(x)
+    const double wr = 3.0 * wq(qp) * cp.rho0;                 // w_q / c_s^2 * rho0
     double val;
     bool cli_done = false;
     if (cp.variant >= 1) {
         // second node x - c_qp = x + c_q must be a fluid cell (CLI and MR)
         int x2, y2, z2;
-        shifted<Q>(b, x, y, z, +1, x2, y2, z2);
-        bool ok = !(cz(Q) != 0 && (z2 < 0 || z2 >= g.nz));
+        shifted_rt(b, x, y, z, q, +1, x2, y2, z2);
+        bool ok = !(rcz(q) != 0 && (z2 < 0 || z2 >= g.nz));
         if (ok) ok = owner_of(g, parts, np, gm, x2, y2, z2) == 0;
         if (ok && (x2 < 0 || x2 >= g.nx || y2 < 0 || y2 >= g.ny || z2 < 0 || z2 >= g.nz)) {
             atomicOr(status, ST_BOUNDS);
             ok = false;
         }
         if (ok) {
-            const double f2 = ld_pdf(src + (long long)QP * g.n + lin(g, x2, y2, z2), QP);
-            const double fq = ld_pdf(src + (long long)Q * g.n + idx, Q);
+            const double f2 = ld_pdf(src + (long long)qp * g.n + lin(g, x2, y2, z2), qp);
+            const double fq = ld_pdf(src + (long long)q * g.n + idx, q);
             bool mr_done = false;
             if (cp.variant == 2) {
                 // Eq. (15): third node x - 2 c_qp = x + 2 c_q must be fluid too
-                int x3 = x2 + cx(Q), y3 = y2 + cy(Q), z3 = z2 + cz(Q);
+                int x3 = x2 + rcx(q), y3 = y2 + rcy(q), z3 = z2 + rcz(q);
                 x3 = x3 < 0 ? x3 + g.nx : (x3 >= g.nx ? x3 - g.nx : x3);
                 y3 = y3 < 0 ? y3 + g.ny : (y3 >= g.ny ? y3 - g.ny : y3);
                 bool ok3 = true;
@@ -181,8 +246,8 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
                     ok3 = false;
                 }
                 if (ok3) {
-                    const double f3 = ld_pdf(src + (long long)QP * g.n + lin(g, x3, y3, z3), QP);
-                    const double fq2 = ld_pdf(src + (long long)Q * g.n + lin(g, x2, y2, z2), Q);
+                    const double f3 = ld_pdf(src + (long long)qp * g.n + lin(g, x3, y3, z3), qp);
+                    const double fq2 = ld_pdf(src + (long long)q * g.n + lin(g, x2, y2, z2), q);
                     own_momentum(src, g, idx, mc);
                     const double d1 = (1.0 + delta) * (1.0 + delta);
                     const double k0 = (1.0 - 2.0 * delta - 2.0 * delta * delta) / d1;
@@ -190,8 +255,7 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
                     const double alpha = 4.0 / d1;
                     // (1 - |lambda_-|) n^-_qp(x, t), rebuilt from the stored values
                     const double odd = 0.5 * (ftqp - fq) -
-                                       3.0 * wq(QP) *
-                                           (cx(QP) * mc.j[0] + cy(QP) * mc.j[1] + cz(QP) * mc.j[2]);
+                                       3.0 * wq(qp) * (cqx * mc.j[0] + cqy * mc.j[1] + cqz * mc.j[2]);
                     val = ftqp + k0 * (f2 - fq) + km1 * (f3 - fq2) - alpha * wr * vc +
                           cp.mr_cpc / d1 * odd;
                     mr_done = true;
@@ -206,48 +270,159 @@ __device__ __forceinline__ void mem_pull_one(const T* __restrict__ src, const Ge
         }
     }
     if (!cli_done) val = ftqp - 2.0 * wr * vc;
-    f[Q] = (C)val;
-    if (slots) {
+    if (ft) {
         double F[3], arm[3], Tq[3];
-        F[0] = (cx(QP) - v[0]) * ftqp - (cx(Q) - v[0]) * val;
-        F[1] = (cy(QP) - v[1]) * ftqp - (cy(Q) - v[1]) * val;
-        F[2] = (cz(QP) - v[2]) * ftqp - (cz(Q) - v[2]) * val;
+        F[0] = (cqx - v[0]) * ftqp - (-cqx - v[0]) * val;
+        F[1] = (cqy - v[1]) * ftqp - (-cqy - v[1]) * val;
+        F[2] = (cqz - v[2]) * ftqp - (-cqz - v[2]) * val;
         separation(g, xb[0], xb[1], xb[2], P, arm[0], arm[1], arm[2]);
         cross3(arm, F, Tq);
-        if (!slots->add(owner - 1, F, Tq)) atomicOr(status, ST_TOO_MANY_OBJECTS);
+        ft[0] = F[0];
+        ft[1] = F[1];
+        ft[2] = F[2];
+        ft[3] = Tq[0];
+        ft[4] = Tq[1];
+        ft[5] = Tq[2];
+        *owner_out = owner;
     }
+    return val;
 }
 
-template <typename T, typename C, int Q>
-struct MemPull {
-    __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
-                                               const Coupl& cp, const DevParticle* parts, int np,
-                                               const GeoMap* gm, const Nbr& b, int x, int y, int z,
-                                               long long idx, C (&f)[NQ], Slots* slots,
-                                               int* status, MrCell& mc) {
-        mem_pull_one<T, C, Q>(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status, mc);
-        MemPull<T, C, Q + 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status,
-                                  mc);
+template <typename C, int Q>
+struct MemMerge {
+    __device__ __forceinline__ static void run(unsigned cut, const double (&lv)[NQ], C (&f)[NQ]) {
+        if ((cut >> Q) & 1u) f[Q] = (C)lv[Q];
+        MemMerge<C, Q + 1>::run(cut, lv, f);
     }
 };
-template <typename T, typename C>
-struct MemPull<T, C, NQ> {
-    __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const Coupl&,
-                                               const DevParticle*, int, const GeoMap*, const Nbr&,
-                                               int, int, int, long long, C (&)[NQ], Slots*, int*,
-                                               MrCell&) {}
+template <typename C>
+struct MemMerge<C, NQ> {
+    __device__ __forceinline__ static void run(unsigned, const double (&)[NQ], C (&)[NQ]) {}
 };
 
+// MEM pull for a fluid cell: stream Eq. (2) on every link whose upstream cell
+// is fluid (phase 1, unrolled), then the boundary values of the cut links in a
+// loop over them (phase 2, one copy of the link code, links in increasing q).
 template <typename T, typename C>
 __device__ __forceinline__ void mem_pull(const T* __restrict__ src, const Geom& g, const Coupl& cp,
                                          const DevParticle* parts, int np, const GeoMap* gm,
                                          int x, int y, int z, long long idx, C (&f)[NQ],
                                          Slots* slots, int* status) {
     Nbr b = make_nbr(g, x, y, z);
-    MrCell mc;
-    mc.have = false;
     f[0] = PdfStore<T>::template load<C>(src + idx, 0);
-    MemPull<T, C, 1>::run(src, g, cp, parts, np, gm, b, x, y, z, idx, f, slots, status, mc);
+    unsigned cut = 0;
+    MemPull<T, C, 1>::run(src, g, parts, np, gm, b, x, y, z, idx, f, cut, status);
+    if (cut) {
+        double lv[NQ];
+        MrCell mc;
+        mc.have = false;
+        for (unsigned m = cut; m; m &= m - 1) {
+            const int q = __ffs(m) - 1;
+            double ft[6];
+            int owner = 0;
+            lv[q] = mem_link(src, g, cp, parts, np, gm, b, x, y, z, idx, q, slots ? ft : nullptr,
+                             &owner, status, mc);
+            if (slots && owner) {
+                const double F[3] = {ft[0], ft[1], ft[2]}, Tq[3] = {ft[3], ft[4], ft[5]};
+                if (!slots->add(owner - 1, F, Tq)) atomicOr(status, ST_TOO_MANY_OBJECTS);
+            }
+        }
+        MemMerge<C, 1>::run(cut, lv, f);
+    }
+}
+
+// Per-warp scratch of the warp-cooperative MEM link loop.
+struct LinkWarp {
+    double lv[NQ * 32];            // link values, in list order
+    double ft[32][6];              // force and torque of the links of one round
+    double jt[32][3];              // MR: post-collision momentum of each lane's cell
+    long long idx[32];
+    int x[32], y[32], z[32], own[32];
+    unsigned short list[NQ * 32];  // (lane << 5) | q, lanes in order, q ascending
+};
+
+template <typename C, int Q>
+struct WarpMerge {
+    __device__ __forceinline__ static void run(unsigned cut, const double* lv, int k, C (&f)[NQ]) {
+        if ((cut >> Q) & 1u) f[Q] = (C)lv[k++];
+        WarpMerge<C, Q + 1>::run(cut, lv, k, f);
+    }
+};
+template <typename C>
+struct WarpMerge<C, NQ> {
+    __device__ __forceinline__ static void run(unsigned, const double*, int, C (&)[NQ]) {}
+};
+
+// Warp-cooperative phase 2 for the near sweep (all 32 lanes call it): the cut
+// links of the warp's cells are listed in lane order and spread over the lanes
+// 32 at a time, so a boundary cell with many links no longer holds up its
+// warp.  Each cell then adds the forces of its own links in ascending q (the
+// order of the per-cell loop) and takes its link values.
+template <typename T, typename C>
+__device__ __forceinline__ void mem_links_warp(const T* __restrict__ src, const Geom& g,
+                                               const Coupl& cp, const DevParticle* parts,
+                                               const GeoMap* gm, int x, int y, int z, long long idx,
+                                               unsigned cut, C (&f)[NQ], Slots& slots, int* status,
+                                               LinkWarp& w, int lane) {
+    const unsigned full = 0xffffffffu;
+    const int nl = __popc(cut);
+    int inc = nl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(full, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const int total = __shfl_sync(full, inc, 31);
+    if (total == 0) return;  // warp-uniform
+    const int first = inc - nl;
+    int k = first;
+    for (unsigned m = cut; m; m &= m - 1) w.list[k++] = (unsigned short)((lane << 5) | (__ffs(m) - 1));
+    w.x[lane] = x;
+    w.y[lane] = y;
+    w.z[lane] = z;
+    w.idx[lane] = idx;
+    if (cut && cp.variant == 2) {
+        MrCell mc;
+        mc.have = false;
+        own_momentum(src, g, idx, mc);
+        w.jt[lane][0] = mc.j[0];
+        w.jt[lane][1] = mc.j[1];
+        w.jt[lane][2] = mc.j[2];
+    }
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+        const int e = base + lane;
+        w.own[lane] = 0;
+        if (e < total) {
+            const int ol = w.list[e] >> 5, q = w.list[e] & 31;
+            const int lx = w.x[ol], ly = w.y[ol], lz = w.z[ol];
+            const Nbr b = make_nbr(g, lx, ly, lz);
+            MrCell mc;
+            mc.have = cp.variant == 2;
+            if (mc.have) {
+                mc.j[0] = w.jt[ol][0];
+                mc.j[1] = w.jt[ol][1];
+                mc.j[2] = w.jt[ol][2];
+            }
+            w.lv[e] = mem_link(src, g, cp, parts, cp.np, gm, b, lx, ly, lz, w.idx[ol], q,
+                               &w.ft[lane][0], &w.own[lane], status, mc);
+        }
+        __syncwarp();
+        // this round's links of this lane's cell: entries [lo, hi)
+        const int lo = first > base ? first : base;
+        const int hi = (first + nl) < (base + 32) ? (first + nl) : (base + 32);
+        for (int e2 = lo; e2 < hi; ++e2) {
+            const int s = e2 - base;
+            if (w.own[s]) {
+                const double F[3] = {w.ft[s][0], w.ft[s][1], w.ft[s][2]};
+                const double Tq[3] = {w.ft[s][3], w.ft[s][4], w.ft[s][5]};
+                if (!slots.add(w.own[s] - 1, F, Tq)) atomicOr(status, ST_TOO_MANY_OBJECTS);
+            }
+        }
+        __syncwarp();
+    }
+    WarpMerge<C, 1>::run(cut, w.lv, first, f);
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -523,7 +698,7 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
                                            const DevParticle* sp, const GeoMap& gm,
                                            double* __restrict__ partials, int* __restrict__ status,
                                            int p, int bx, int by, int bzz, long long nblk,
-                                           long long blk, double (*red)[6]) {
+                                           long long blk, double (*red)[6], LinkWarp* lw) {
     const int tid = threadIdx.x + NEAR_BX * (threadIdx.y + NEAR_BY * threadIdx.z);
     constexpr int nthr = NEAR_BX * NEAR_BY * NEAR_BZ;
     const int* R = sp[p].reg;
@@ -547,15 +722,9 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
         const long long idx = lin(g, x, y, z);
         C f[NQ];
         if (KIND == 2) {
-            // MEM: solid cells are not updated (Sec. 2.2)
-            const int own = map_at(gm, p, kx, ky, kz);
-            if (!own) {
-                if (NOSTREAM)
-                    load_own(src, g, idx, f);
-                else if (clear_of_particles(g, sp, cp.np, x, y, z))
-                    pull_plain(src, g, x, y, z, idx, f);  // no solid neighbour, no link
-                else
-                    mem_pull(src, g, cp, sp, cp.np, &gm, x, y, z, idx, f, &slots, status);
+            // MEM with no stream (first sweep after set-up): fluid cells collide
+            if (NOSTREAM && !map_at(gm, p, kx, ky, kz)) {
+                load_own(src, g, idx, f);
                 collide_fluid(f, k);
                 store_own(dst, g, idx, f);
             }
@@ -588,6 +757,31 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
                 collide_fluid(f, k);
             else
                 psm_collide(f, k, cp, g, sp, nobj, pid, eps, x, y, z, slots);
+            store_own(dst, g, idx, f);
+        }
+    }
+    if (KIND == 2 && !NOSTREAM) {
+        // MEM (Sec. 2.2): solid cells are not updated; every lane of the warp
+        // takes part in the link loop, cells or not
+        C f[NQ];
+        bool fluid = false;
+        long long idx = 0;
+        unsigned cut = 0;
+        if (active && !map_at(gm, p, kx, ky, kz)) {
+            fluid = true;
+            idx = lin(g, x, y, z);
+            if (clear_of_particles(g, sp, cp.np, x, y, z)) {
+                pull_plain(src, g, x, y, z, idx, f);  // no solid neighbour, no link
+            } else {
+                const Nbr b = make_nbr(g, x, y, z);
+                f[0] = PdfStore<T>::template load<C>(src + idx, 0);
+                MemPull<T, C, 1>::run(src, g, sp, cp.np, &gm, b, x, y, z, idx, f, cut, status);
+            }
+        }
+        mem_links_warp(src, g, cp, sp, &gm, x, y, z, idx, cut, f, slots, status, lw[tid >> 5],
+                       tid & 31);
+        if (fluid) {
+            collide_fluid(f, k);
             store_own(dst, g, idx, f);
         }
     }
@@ -624,6 +818,7 @@ __global__ void __launch_bounds__(256)
            int* __restrict__ status, int bz) {
     __shared__ DevParticle sp[MAX_PARTICLES];
     __shared__ double red[8][6];
+    __shared__ LinkWarp lw[KIND == 2 ? NEAR_BX * NEAR_BY * NEAR_BZ / 32 : 1];
     const int tid = threadIdx.x + NEAR_BX * (threadIdx.y + NEAR_BY * threadIdx.z);
     constexpr int nthr = NEAR_BX * NEAR_BY * NEAR_BZ;
     for (int i = tid; i < cp.np * (int)(sizeof(DevParticle) / sizeof(double)); i += nthr)
@@ -633,7 +828,7 @@ __global__ void __launch_bounds__(256)
     const long long nblk = (long long)gridDim.x * gridDim.y * bz;
     const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * bzz);
     near_block<T, C, KIND, NOSTREAM>(src, dst, g, k, cp, sp, gm, partials, status, p, blockIdx.x,
-                                     blockIdx.y, bzz, nblk, blk, red);
+                                     blockIdx.y, bzz, nblk, blk, red, lw);
 }
 
 // ---------------------------------------------------------------------------
@@ -1160,6 +1355,7 @@ __global__ void __launch_bounds__(256)
     k_batch_near(BatchCase* __restrict__ cases, BatchList l, int sub, int* __restrict__ status) {
     __shared__ DevParticle sp[1];
     __shared__ double red[8][6];
+    __shared__ LinkWarp lw[NEAR_BX * NEAR_BY * NEAR_BZ / 32];
     const int i = find_item(l.base, l.n, blockIdx.x);
     const BatchCase& B = cases[l.list[i]];
     const long long local = blockIdx.x - l.base[i];
@@ -1175,10 +1371,12 @@ __global__ void __launch_bounds__(256)
     double* partials = B.partials + (long long)sub * B.nblk * 6;
     if (B.kind == 2)
         near_block<double, double, 2, false>(B.buf[cur], B.buf[1 - cur], B.g, B.kd, B.cp, sp, gm,
-                                             partials, status, 0, bx, by, bzz, B.nblk, local, red);
+                                             partials, status, 0, bx, by, bzz, B.nblk, local, red,
+                                             lw);
     else
         near_block<double, double, 1, false>(B.buf[cur], B.buf[1 - cur], B.g, B.kd, B.cp, sp, gm,
-                                             partials, status, 0, bx, by, bzz, B.nblk, local, red);
+                                             partials, status, 0, bx, by, bzz, B.nblk, local, red,
+                                             lw);
 }
 
 // One 256-cell segment of an xy plane of the bulk sweep: cells
