@@ -236,7 +236,10 @@ lbm_status after_pre_state(lbm_handle* h) {
     return LBM_OK;
 }
 
-lbm_status sweep(lbm_handle* h, int sub) {
+// with_map: first sweep of a coupled step; the geometry map of the step's
+// particle state is built on the side stream ahead of the near sweep (k_bulk
+// does not read it, so it hides under the bulk sweep).
+lbm_status sweep(lbm_handle* h, int sub, bool with_map) {
     Launch L = base_launch(h);
     L.nostream = h->pending_pre;
     L.partials = h->d_partials + (size_t)sub * (size_t)near_partial_doubles(L.box, h->np);
@@ -249,6 +252,11 @@ lbm_status sweep(lbm_handle* h, int sub) {
         CK(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
         Launch Ln = L;
         Ln.stream = h->side;
+        if (with_map) {
+            int pm = prof_begin(h, PC_OTHER, h->side);
+            CK(h, launch_map(Ln), "geometry map launch");
+            prof_end(h, pm, h->side);
+        }
         int pn = prof_begin(h, PC_NEAR, h->side);
         CK(h, launch_near(h->storage, src, dst, Ln), "near sweep launch");
         prof_end(h, pn, h->side);
@@ -267,15 +275,10 @@ lbm_status step_once(lbm_handle* h) {
     lbm_status st;
     const int coupled = h->np > 0 && h->kind != 0;
     const int nsub = h->kind == 2 ? h->subcycles : 1;
-    if (coupled) {
-        // geometry of the current particle state, shared by the step's sweeps
-        Launch L = base_launch(h);
-        int pi = prof_begin(h, PC_OTHER);
-        CK(h, launch_map(L), "geometry map launch");
-        prof_end(h, pi);
-    }
+    // the geometry of the current particle state, shared by the step's
+    // sweeps, is built by the first sweep (side stream)
     for (int s = 0; s < nsub; ++s)
-        if ((st = sweep(h, s)) != LBM_OK) return st;
+        if ((st = sweep(h, s, coupled && s == 0)) != LBM_OK) return st;
     if (!coupled) return LBM_OK;
     Launch L = base_launch(h);
     int pi = prof_begin(h, PC_FINAL);
