@@ -9,8 +9,8 @@
 //
 // One global step is captured once as a CUDA graph on a private stream:
 //
-//   map (all cases)
-//   for s < max subcycles:   near (cases with > s sweeps, side branch)
+//   for s < max subcycles:   [s = 0: map (all cases)] -> near (cases with
+//                            > s sweeps, side branch)
 //                            || bulk (same cases, persistent)  -> swap
 //   force total -> rigid-body update (all cases) -> refill (MEM cases)
 //
@@ -186,15 +186,19 @@ void destroy_graph(lbm_batch* b) {
 cudaError_t enqueue_step(lbm_batch* b, int* kernels) {
     cudaStream_t s = b->cap;
     int k = 0;
-    cudaError_t e = launch_batch_map(b->dcases, b->map_l.view(), b->map_l.total, s);
-    ++k;
+    cudaError_t e = cudaSuccess;
     for (int sub = 0; sub < b->max_sub && e == cudaSuccess; ++sub) {
         const WorkList& nl = b->near_l[sub];
         const WorkList& bl = b->bulk_l[sub];
         // near-particle and bulk cells are disjoint: the near sweep is a
-        // parallel branch of the graph
+        // parallel branch of the graph; the first one builds the step's
+        // geometry map first (the bulk sweep does not read it)
         e = cudaEventRecord(b->ev_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+        if (e == cudaSuccess && sub == 0) {
+            e = launch_batch_map(b->dcases, b->map_l.view(), b->map_l.total, b->side);
+            ++k;
+        }
         if (e == cudaSuccess) e = launch_batch_near(b->dcases, nl.view(), nl.total, sub, b->dstatus, b->side);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
         if (e == cudaSuccess) e = launch_batch_bulk(b->mode, b->dcases, bl.view(), bl.total, b->grid, s);

@@ -1005,8 +1005,9 @@ __global__ void k_regions(Geom g, DevParticle* parts, int np) {
 
 // ---------------------------------------------------------------------------
 // MEM re-mapping with PDF reconstruction (Sec. 2.2, Eq. (19)).  One thread per
-// cell of the box around each particle's old position.  A cell solid under
-// p_old (owner p) and fluid under p_new gets:
+// cell of the box around each particle's old position finds the candidates: a
+// cell solid under p_old (owner p) and fluid under p_new.  Each candidate is
+// then rebuilt by its whole warp (refill_warp) and gets:
 //   extrapolate = 1: f = 3 f(x+c_n) - 3 f(x+2c_n) + f(x+3c_n) (fewer terms when
 //     fewer usable fluid cells follow), with the pre-collision values of those
 //     cells rebuilt from srcB (the buffer the last sweep pulled from) under
@@ -1014,29 +1015,56 @@ __global__ void k_regions(Geom g, DevParticle* parts, int np) {
 //     f_eq(rho_bar, v);
 //   extrapolate = 0: f_eq(rho0, v);
 // and is then collided (plain fluid collision) into dst.
+
+// Pre-collision value f_q(x) of one direction q (known at run time) of a
+// fluid cell x, as mem_pull rebuilds it (particle owners from the records).
 template <typename T, typename C>
-__device__ __forceinline__ void refill_cell(const T* __restrict__ srcB, T* __restrict__ dst,
+__device__ __forceinline__ C mem_pull_dir(const T* __restrict__ src, const Geom& g, const Coupl& cp,
+                                          const DevParticle* parts, int x, int y, int z, int q,
+                                          int* status) {
+    const long long idx = lin(g, x, y, z);
+    if (q == 0) return PdfStore<T>::template load<C>(src + idx, 0);
+    const Nbr b = make_nbr(g, x, y, z);
+    const int qp = opp(q);
+    int xs, ys, zs;
+    shifted_rt(b, x, y, z, q, -1, xs, ys, zs);
+    if (rcz(q) != 0 && (zs < 0 || zs >= g.nz))
+        return PdfStore<T>::template load<C>(src + (long long)qp * g.n + idx, qp);
+    const int owner = cell_owner(g, parts, cp.np, xs, ys, zs);
+    if (!owner) {
+        if (xs < 0 || xs >= g.nx || ys < 0 || ys >= g.ny || zs < 0 || zs >= g.nz) {
+            atomicOr(status, ST_BOUNDS);
+            return (C)0.0;
+        }
+        return PdfStore<T>::template load<C>(src + (long long)q * g.n + lin(g, xs, ys, zs), q);
+    }
+    if (owner < 0 || owner > cp.np) {
+        atomicOr(status, ST_BOUNDS);
+        return (C)0.0;
+    }
+    MrCell mc;
+    mc.have = false;
+    int unused = 0;
+    return (C)mem_link(src, g, cp, parts, cp.np, (const GeoMap*)nullptr, b, x, y, z, idx, q,
+                       (double*)nullptr, &unused, status, mc);
+}
+
+// Per-warp scratch of the refill.
+struct RefillWarp {
+    double f[3][NQ];  // pre-collision values of the extrapolation cells
+    double r[NQ];     // densities of the usable neighbours (no extrapolation cell)
+    int ok[NQ];
+};
+
+// Rebuilds candidate cell (x, y, z) of particle p; all 32 lanes call it with
+// the same cell.  The pulls are spread over the lanes, the rest is computed
+// by every lane alike and lane 0 stores.
+template <typename T, typename C>
+__device__ __forceinline__ void refill_warp(const T* __restrict__ srcB, T* __restrict__ dst,
                                             const Geom& g, const Coll<C>& k, const Coupl& cp,
                                             const DevParticle* so, const DevParticle* sn,
-                                            int extrapolate, int side, int p, long long lid,
-                                            int* __restrict__ status) {
-    if (lid >= (long long)side * side * side) return;
-    const int kx = (int)(lid % side), ky = (int)((lid / side) % side),
-              kz = (int)(lid / ((long long)side * side));
-    const DevParticle& Po = so[p];
-    int x = (int)floor(Po.x[0] - Po.r) - 1 + kx;
-    int y = (int)floor(Po.x[1] - Po.r) - 1 + ky;
-    int z = (int)floor(Po.x[2] - Po.r) - 1 + kz;
-    x = wrap_i(x, g.nx);
-    y = wrap_i(y, g.ny);
-    if (g.bc_z) {
-        if (z < 0 || z >= g.nz) return;
-    } else {
-        z = wrap_i(z, g.nz);
-    }
-    if (cell_owner(g, so, cp.np, x, y, z) != p + 1) return;
-    if (cell_owner(g, sn, cp.np, x, y, z) != 0) return;
-
+                                            int extrapolate, int p, int x, int y, int z,
+                                            int* __restrict__ status, RefillWarp& w, int lane) {
     const DevParticle& Pn = sn[p];
     const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
     double v[3];
@@ -1076,26 +1104,23 @@ __device__ __forceinline__ void refill_cell(const T* __restrict__ srcB, T* __res
         }
     }
     if (m > 0) {
-        C f1[NQ];
-        mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, nbx[0], nby[0], nbz[0], lin(g, nbx[0], nby[0], nbz[0]),
-                 f1, (Slots*)nullptr, status);
+        // the m x 19 pulls, lane by lane
+        for (int i = lane; i < m * NQ; i += 32) {
+            const int jn = i / NQ, q = i - jn * NQ;
+            w.f[jn][q] =
+                (double)mem_pull_dir<T, C>(srcB, g, cp, so, nbx[jn], nby[jn], nbz[jn], q, status);
+        }
+        __syncwarp();
         if (m == 1) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) fn[q] = f1[q];
+            for (int q = 0; q < NQ; ++q) fn[q] = (C)w.f[0][q];
+        } else if (m == 2) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) fn[q] = (C)2 * (C)w.f[0][q] - (C)w.f[1][q];
         } else {
-            C f2[NQ];
-            mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, nbx[1], nby[1], nbz[1],
-                     lin(g, nbx[1], nby[1], nbz[1]), f2, (Slots*)nullptr, status);
-            if (m == 2) {
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) fn[q] = (C)2 * f1[q] - f2[q];
-            } else {
-                C f3[NQ];
-                mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, nbx[2], nby[2], nbz[2],
-                         lin(g, nbx[2], nby[2], nbz[2]), f3, (Slots*)nullptr, status);
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) fn[q] = (C)3 * f1[q] - (C)3 * f2[q] + f3[q];
-            }
+            for (int q = 0; q < NQ; ++q)
+                fn[q] = (C)3 * (C)w.f[0][q] - (C)3 * (C)w.f[1][q] + (C)w.f[2][q];
         }
         // velocity constraint: only the momentum moment changes (sum_q c_qa^2 = 10)
         double j[3] = {0.0, 0.0, 0.0};
@@ -1113,24 +1138,32 @@ __device__ __forceinline__ void refill_cell(const T* __restrict__ srcB, T* __res
     } else {
         double rbar = cp.rho0;
         if (extrapolate) {
+            // lane q - 1 pulls neighbour x + c_q (q = 1..18) when it is usable
+            if (lane < NQ - 1) {
+                const int q = lane + 1;
+                int xx = wrap_i(x + rcx(q), g.nx), yy = wrap_i(y + rcy(q), g.ny), zz = z + rcz(q);
+                bool ok = true;
+                if (g.bc_z) ok = zz >= 0 && zz < g.nz;
+                else zz = wrap_i(zz, g.nz);
+                if (ok)
+                    ok = !cell_owner(g, so, cp.np, xx, yy, zz) && !cell_owner(g, sn, cp.np, xx, yy, zz);
+                double r = 0.0;
+                if (ok) {
+                    C fq[NQ];
+                    mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, xx, yy, zz,
+                             lin(g, xx, yy, zz), fq, (Slots*)nullptr, status);
+#pragma unroll
+                    for (int qq = 0; qq < NQ; ++qq) r += (double)fq[qq];
+                }
+                w.r[q] = r;
+                w.ok[q] = ok ? 1 : 0;
+            }
+            __syncwarp();
             double sum = 0.0;
             int cnt = 0;
             for (int q = 1; q < NQ; ++q) {
-                int xx = wrap_i(x + cx(q), g.nx), yy = wrap_i(y + cy(q), g.ny), zz = z + cz(q);
-                if (g.bc_z) {
-                    if (zz < 0 || zz >= g.nz) continue;
-                } else {
-                    zz = wrap_i(zz, g.nz);
-                }
-                if (cell_owner(g, so, cp.np, xx, yy, zz) || cell_owner(g, sn, cp.np, xx, yy, zz))
-                    continue;
-                C fq[NQ];
-                mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, xx, yy, zz, lin(g, xx, yy, zz), fq,
-                         (Slots*)nullptr, status);
-                double r = 0.0;
-#pragma unroll
-                for (int qq = 0; qq < NQ; ++qq) r += (double)fq[qq];
-                sum += r;
+                if (!w.ok[q]) continue;
+                sum += w.r[q];
                 ++cnt;
             }
             if (cnt > 0) rbar = sum / cnt;
@@ -1138,11 +1171,50 @@ __device__ __forceinline__ void refill_cell(const T* __restrict__ srcB, T* __res
         equilibrium((C)rbar, (C)v[0], (C)v[1], (C)v[2], k.rho0, fn);
     }
     collide_fluid(fn, k);
-    if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz) {
-        atomicOr(status, ST_BOUNDS);
-        return;
+    if (lane == 0) {
+        if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)
+            atomicOr(status, ST_BOUNDS);
+        else
+            store_own(dst, g, lin(g, x, y, z), fn);
     }
-    store_own(dst, g, lin(g, x, y, z), fn);
+    __syncwarp();
+}
+
+// Candidate test of thread lid of particle p's box, then the warp's
+// candidates one after another.  Every lane of the warp must call this.
+template <typename T, typename C>
+__device__ __forceinline__ void refill_cells(const T* __restrict__ srcB, T* __restrict__ dst,
+                                             const Geom& g, const Coll<C>& k, const Coupl& cp,
+                                             const DevParticle* so, const DevParticle* sn,
+                                             int extrapolate, int side, int p, long long lid,
+                                             int* __restrict__ status, RefillWarp& w, int lane) {
+    bool cand = lid < (long long)side * side * side;
+    int x = 0, y = 0, z = 0;
+    if (cand) {
+        const int kx = (int)(lid % side), ky = (int)((lid / side) % side),
+                  kz = (int)(lid / ((long long)side * side));
+        const DevParticle& Po = so[p];
+        x = (int)floor(Po.x[0] - Po.r) - 1 + kx;
+        y = (int)floor(Po.x[1] - Po.r) - 1 + ky;
+        z = (int)floor(Po.x[2] - Po.r) - 1 + kz;
+        x = wrap_i(x, g.nx);
+        y = wrap_i(y, g.ny);
+        if (g.bc_z) {
+            if (z < 0 || z >= g.nz) cand = false;
+        } else {
+            z = wrap_i(z, g.nz);
+        }
+    }
+    if (cand) cand = cell_owner(g, so, cp.np, x, y, z) == p + 1;
+    if (cand) cand = cell_owner(g, sn, cp.np, x, y, z) == 0;
+    const unsigned full = 0xffffffffu;
+    for (unsigned m = __ballot_sync(full, cand); m; m &= m - 1) {
+        const int src_lane = __ffs(m) - 1;
+        const int cxl = __shfl_sync(full, x, src_lane), cyl = __shfl_sync(full, y, src_lane),
+                  czl = __shfl_sync(full, z, src_lane);
+        refill_warp<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, p, cxl, cyl, czl, status, w,
+                          lane);
+    }
 }
 
 template <typename T, typename C>
@@ -1158,8 +1230,9 @@ __global__ void __launch_bounds__(128)
         reinterpret_cast<double*>(sn)[i] = reinterpret_cast<const double*>(p_new)[i];
     }
     __syncthreads();
-    refill_cell<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, side, blockIdx.y,
-                      (long long)blockIdx.x * blockDim.x + tid, status);
+    __shared__ RefillWarp rw[4];
+    refill_cells<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, side, blockIdx.y,
+                       (long long)blockIdx.x * blockDim.x + tid, status, rw[tid >> 5], tid & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -1468,8 +1541,10 @@ __global__ void __launch_bounds__(128)
     }
     __syncthreads();
     const int cur = B.cur;
-    refill_cell<double, double>(B.buf[1 - cur], B.buf[cur], B.g, B.kd, B.cp, so, sn, 1,
-                                B.refill_side, 0, local * blockDim.x + threadIdx.x, status);
+    __shared__ RefillWarp rw[4];
+    refill_cells<double, double>(B.buf[1 - cur], B.buf[cur], B.g, B.kd, B.cp, so, sn, 1,
+                                 B.refill_side, 0, local * blockDim.x + threadIdx.x, status,
+                                 rw[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
