@@ -307,15 +307,16 @@ enum {
 
 /* Creates a batch of n_cases (1..4096) cases.
  *   cfgs[c]       configuration of case c (as for lbm_create); coupling must
- *                 be a PSM variant, LBM_MEM_BB or LBM_MEM_CLI; storage must
- *                 be LBM_STORE_F64 or LBM_STORE_F64_FX and the same for every
- *                 case.
+ *                 be a PSM or MEM variant (LBM_MEM_MR as for lbm_create);
+ *                 bc_z 0 or 1; storage must be LBM_STORE_F64 or
+ *                 LBM_STORE_F64_FX and the same for every case.
  *   particles[c]  the one sphere of case c (copied).
  *   stream        cudaStream_t or NULL: stream of every batch call.
  * All device memory of the batch is one allocation (PDF buffers, particle
  * records, force partials and geometry maps, 256-byte aligned slices).
- * Returns LBM_ERR_ARG for an invalid case (nothing is allocated),
- * LBM_ERR_OOM when the allocation fails. */
+ * Returns LBM_ERR_ARG for an invalid case, LBM_ERR_UNSUPPORTED for a valid
+ * but unsupported one (nothing is allocated; lbm_batch_last_error(NULL) says
+ * which case and why), LBM_ERR_OOM when the allocation fails. */
 lbm_status lbm_batch_create(int n_cases, const lbm_config *cfgs, const lbm_particle *particles,
                             void *stream, lbm_batch **out);
 
