@@ -85,6 +85,7 @@ struct Coll {
     int has_force;
     // folded constants of the pair update (see collide_fluid)
     C alpha, beta;    // 1 + (l+ + l-)/2, (l+ - l-)/2
+    C hs, hd;         // (alpha + beta)/2 = (1 + l+)/2, (alpha - beta)/2 = (1 + l-)/2
     C c0;             // 1 + l+
     C m15r0;          // -3/2 rho0
     C lpw[3];         // l+ w_k, k = rest, axis, diagonal
@@ -519,6 +520,11 @@ __device__ __forceinline__ void moments(const C (&f)[NQ], const Coll<C>& k, C& r
 //   f_qbar' = alpha f_qbar + beta f_q    - (P - M)
 // with P = l+ f^eq,+ - F^+ and M = l- f^eq,- - F^-, which expands
 // f_q + l+ (f_q^+ - f^eq,+) + l- (f_q^- - f^eq,-) + F_q exactly.
+// Arithmetic whose products cost far more than its sums (the 64-bit fixed
+// point) takes the pair update in sum / difference form,
+//   f_q' = hs (f_q + f_qbar) + hd (f_q - f_qbar) - (P + M),
+//   f_qbar' = hs (f_q + f_qbar) - hd (f_q - f_qbar) - (P - M):
+// two products per pair instead of four (PairSumDiff, lbm_fixed.cuh).
 template <typename C, int Q, int K, bool FORCE>
 __device__ __forceinline__ void trt_pair(C (&f)[NQ], C cu, const C (&bw)[3], const Coll<C>& k) {
     constexpr int QB = Q + 1;
@@ -526,8 +532,14 @@ __device__ __forceinline__ void trt_pair(C (&f)[NQ], C cu, const C (&bw)[3], con
                 : fma(k.k1w[K], cu * cu, bw[K]);
     C M = FORCE ? fma(k.k2w[K], cu, -k.fq[(Q - 1) / 2]) : k.k2w[K] * cu;
     const C a = f[Q], b = f[QB];
-    f[Q] = fma(k.alpha, a, fma(k.beta, b, -(P + M)));
-    f[QB] = fma(k.alpha, b, fma(k.beta, a, -(P - M)));
+    if constexpr (PairSumDiff<C>::value) {
+        const C sp = k.hs * (a + b), sd = k.hd * (a - b);
+        f[Q] = (sp + sd) - (P + M);
+        f[QB] = (sp - sd) - (P - M);
+    } else {
+        f[Q] = fma(k.alpha, a, fma(k.beta, b, -(P + M)));
+        f[QB] = fma(k.alpha, b, fma(k.beta, a, -(P - M)));
+    }
 }
 
 template <typename C, bool FORCE>

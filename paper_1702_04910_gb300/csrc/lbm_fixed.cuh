@@ -100,4 +100,10 @@ __device__ __forceinline__ fx64 operator*(fx64 a, fx64 b) {
 
 __device__ __forceinline__ fx64 fma(fx64 a, fx64 b, fx64 c) { return a * b + c; }
 
+// Whether the TRT pair update of arithmetic C takes its sum / difference form
+// (see trt_pair): yes for the fixed point, where a product costs ~15 integer
+// instructions and a sum two.
+template <typename C> struct PairSumDiff { static constexpr bool value = false; };
+template <> struct PairSumDiff<fx64> { static constexpr bool value = true; };
+
 }  // namespace lbmgpu

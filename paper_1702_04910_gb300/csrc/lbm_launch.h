@@ -136,6 +136,8 @@ inline Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) 
     k.has_force = (fe[0] != 0.0 || fe[1] != 0.0 || fe[2] != 0.0);
     k.alpha = (C)(1.0 + 0.5 * (lp + lm));
     k.beta = (C)(0.5 * (lp - lm));
+    k.hs = (C)(0.5 * (1.0 + lp));
+    k.hd = (C)(0.5 * (1.0 + lm));
     k.c0 = (C)(1.0 + lp);
     k.m15r0 = (C)(-1.5 * rho0);
     const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
