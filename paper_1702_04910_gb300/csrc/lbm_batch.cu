@@ -124,7 +124,7 @@ long long map_items(const BatchCase& c) {
 
 long long refill_items(const BatchCase& c) {
     const long long s = c.refill_side;
-    return (s * s * s + 127) / 128;
+    return (s * s * s + REFILL_THREADS - 1) / REFILL_THREADS;
 }
 
 void fill_list(WorkList& w, const std::vector<int>& cases, const std::vector<long long>& items) {

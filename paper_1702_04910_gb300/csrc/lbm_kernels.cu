@@ -1218,7 +1218,7 @@ __device__ __forceinline__ void refill_cells(const T* __restrict__ srcB, T* __re
 }
 
 template <typename T, typename C>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(REFILL_THREADS)
     k_refill(const T* __restrict__ srcB, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
              const DevParticle* __restrict__ p_old, const DevParticle* __restrict__ p_new,
              int extrapolate, int side, int* __restrict__ status) {
@@ -1230,7 +1230,7 @@ __global__ void __launch_bounds__(128)
         reinterpret_cast<double*>(sn)[i] = reinterpret_cast<const double*>(p_new)[i];
     }
     __syncthreads();
-    __shared__ RefillWarp rw[4];
+    __shared__ RefillWarp rw[REFILL_THREADS / 32];
     refill_cells<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, side, blockIdx.y,
                        (long long)blockIdx.x * blockDim.x + tid, status, rw[tid >> 5], tid & 31);
 }
@@ -1529,7 +1529,7 @@ __global__ void k_batch_rigid(BatchCase* __restrict__ cases, int n, int* __restr
 
 // MEM re-mapping and refilling after the step (reads the buffer the last
 // sweep pulled from, writes the stored state)
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(REFILL_THREADS)
     k_batch_refill(BatchCase* __restrict__ cases, BatchList l, int* __restrict__ status) {
     __shared__ DevParticle so[1], sn[1];
     const int i = find_item(l.base, l.n, blockIdx.x);
@@ -1541,7 +1541,7 @@ __global__ void __launch_bounds__(128)
     }
     __syncthreads();
     const int cur = B.cur;
-    __shared__ RefillWarp rw[4];
+    __shared__ RefillWarp rw[REFILL_THREADS / 32];
     refill_cells<double, double>(B.buf[1 - cur], B.buf[cur], B.g, B.kd, B.cp, so, sn, 1,
                                  B.refill_side, 0, local * blockDim.x + threadIdx.x, status,
                                  rw[threadIdx.x >> 5], threadIdx.x & 31);
@@ -1634,8 +1634,8 @@ cudaError_t refill_t(const void* srcB, void* dst, const Launch& L, const DevPart
     if (L.cp.np <= 0) return cudaSuccess;
     int side = L.box[0];  // set by the caller: cube side in cells
     long long cells = (long long)side * side * side;
-    dim3 grid((unsigned)((cells + 127) / 128), L.cp.np, 1);
-    k_refill<T, C><<<grid, 128, 0, L.stream>>>((const T*)srcB, (T*)dst, L.g, coll_of<C, C>(L),
+    dim3 grid((unsigned)((cells + REFILL_THREADS - 1) / REFILL_THREADS), L.cp.np, 1);
+    k_refill<T, C><<<grid, REFILL_THREADS, 0, L.stream>>>((const T*)srcB, (T*)dst, L.g, coll_of<C, C>(L),
                                                 L.cp, po, pn, extrapolate, side, L.status);
     return cudaGetLastError();
 }
@@ -1823,7 +1823,7 @@ cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_
 cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, int* status,
                                 cudaStream_t s) {
     if (l.n == 0 || total == 0) return cudaSuccess;
-    k_batch_refill<<<(unsigned)total, 128, 0, s>>>(cases, l, status);
+    k_batch_refill<<<(unsigned)total, REFILL_THREADS, 0, s>>>(cases, l, status);
     return cudaGetLastError();
 }
 int batch_bulk_blocks_per_sm(int mode) {

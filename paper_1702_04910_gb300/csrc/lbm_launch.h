@@ -36,6 +36,10 @@ struct Launch {
 // Near-kernel block shape and grid: a particle's cell region spans at most
 // D + 2 NEAR_HALO + 1 cells per axis; the grid covers ceil(D) + 6 cells.
 constexpr int NEAR_BX = 32, NEAR_BY = 2, NEAR_BZ = 1;
+// threads per block of the refill kernels (whole warps: a warp rebuilds a cell)
+constexpr int REFILL_THREADS = 128;
+static_assert(NEAR_BX * NEAR_BY * NEAR_BZ % 32 == 0, "near blocks are whole warps");
+static_assert(REFILL_THREADS % 32 == 0, "refill blocks are whole warps");
 
 // Cells per axis of the region box that holds any particle of diameter <= maxd.
 inline void region_extent(const Geom& g, double maxd, int ext[3]) {
