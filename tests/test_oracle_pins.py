@@ -403,6 +403,27 @@ def test_mr_closure_is_exact_for_parabolic_links(delta, Lambda_p, magic):
     assert abs(plain - ftb[i + 1]) > 1e-6
 
 
+@pytest.mark.slow
+def test_mr_coefficients_follow_from_the_symbolic_derivation():
+    """oracle/derive_mr.py re-derives the coefficients of Eq. (15) symbolically
+    (exact steady TRT link recurrence, second-order no-slip conditions); the
+    closure the oracle uses must agree with them at sampled delta, Lambda_-."""
+    sp = pytest.importorskip("sympy")
+    from oracle import derive_mr
+    coef = derive_mr.derive()
+    d, Lm = sp.symbols("delta"), sp.Symbol("Lambda_m", positive=True)
+    rng = np.random.default_rng(17)
+    for delta, lam in ((0.1, 0.3), (0.5, 6.25), (0.93, 1.7)):
+        sub = {d: delta, Lm: lam}
+        v = {k: float(e.subs(sub)) for k, e in coef.items()}
+        f = rng.normal(size=5) * 0.01 + 1.0 / 18.0
+        n_minus, e_wall = 1e-4, 2e-3
+        want = (f[0] + v["kappa_0"] * (f[1] - f[3]) + v["kappa_m1"] * (f[2] - f[4])
+                - v["alpha"] * e_wall + v["k_pc"] * n_minus)
+        got = orc.mr_link(delta, lam, f[0], f[1], f[2], f[3], f[4], n_minus, e_wall)
+        assert abs(got - want) < 1e-15
+
+
 # ---- Fig. 1: drag on a simple-cubic sphere array in Stokes flow ------------------------------
 def _drag_coefficient(coupling, tau, tol=2e-6):
     """C of Sec. 3 (Eq. (30), (31)) on the paper's set-up: L = 32, D = 16,
