@@ -542,10 +542,44 @@ __device__ __forceinline__ void trt_pair(C (&f)[NQ], C cu, const C (&bw)[3], con
     }
 }
 
+// Sum / difference pair update with P given (see trt_pair).
+template <typename C, int Q, int K>
+__device__ __forceinline__ void trt_pair_sd(C (&f)[NQ], C cu, C P, const Coll<C>& k) {
+    constexpr int QB = Q + 1;
+    const C M = k.k2w[K] * cu;
+    const C a = f[Q], b = f[QB];
+    const C sp = k.hs * (a + b), sd = k.hd * (a - b);
+    f[Q] = (sp + sd) - (P + M);
+    f[QB] = (sp - sd) - (P - M);
+}
+
 template <typename C, bool FORCE>
 __device__ __forceinline__ void collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
     C rho, ux, uy, uz;
     moments(f, k, rho, ux, uy, uz);
+    if constexpr (PairSumDiff<C>::value && !FORCE) {
+        // products shared between pairs: with t_a = k1w_diag u_a^2 and
+        // c_ab = k1w_axis u_a u_b (k1w_axis = 2 k1w_diag), the quadratic term
+        // of P is 2 t_a on an axis pair and t_a + t_b +- c_ab on a diagonal one
+        const C xx = ux * ux, yy = uy * uy, zz = uz * uz;
+        const C base = fma(k.m15r0, (xx + yy) + zz, rho);
+        C bw[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bw[c] = k.lpw[c] * base;
+        const C tx = k.k1w[2] * xx, ty = k.k1w[2] * yy, tz = k.k1w[2] * zz;
+        const C cxy = k.k1w[1] * (ux * uy), cxz = k.k1w[1] * (ux * uz), cyz = k.k1w[1] * (uy * uz);
+        f[0] = fma(k.c0, f[0], -bw[0]);
+        trt_pair_sd<C, 1, 1>(f, ux, (tx + tx) + bw[1], k);
+        trt_pair_sd<C, 3, 1>(f, uy, (ty + ty) + bw[1], k);
+        trt_pair_sd<C, 5, 1>(f, uz, (tz + tz) + bw[1], k);
+        trt_pair_sd<C, 7, 2>(f, ux + uy, ((tx + ty) + cxy) + bw[2], k);
+        trt_pair_sd<C, 9, 2>(f, ux - uy, ((tx + ty) - cxy) + bw[2], k);
+        trt_pair_sd<C, 11, 2>(f, ux + uz, ((tx + tz) + cxz) + bw[2], k);
+        trt_pair_sd<C, 13, 2>(f, ux - uz, ((tx + tz) - cxz) + bw[2], k);
+        trt_pair_sd<C, 15, 2>(f, uy + uz, ((ty + tz) + cyz) + bw[2], k);
+        trt_pair_sd<C, 17, 2>(f, uy - uz, ((ty + tz) - cyz) + bw[2], k);
+        return;
+    }
     const C uu = fma(ux, ux, fma(uy, uy, uz * uz));
     const C base = fma(k.m15r0, uu, rho);
     C bw[3];
