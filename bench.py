@@ -35,9 +35,9 @@ METRIC = "MLUPS and % of HBM roofline, coupled D3Q19 step; force/velocity error 
 # k_bulk with FP64 arithmetic is bound by the FP64 pipe (2 FP64 lane-operations
 # per SM per cycle on GB300, ncu peak_sustained): its roofline counts FP64
 # thread-instructions per cell update, measured by ncu on the 128x128x256
-# settling case (profiles/k_bulk_f64_settling_128x128x256.md, per cell the
-# kernel updates), and the DRAM bytes per cell update of the same capture
-# (set to None whenever the kernel changes).
+# settling case (DADD + DFMA + DMUL per cell the kernel updates), and the DRAM
+# bytes per cell update of the same capture (set to None whenever the kernel
+# changes).
 K_BULK_F64_DP_INST_PER_CELL = 127.0
 K_BULK_F64_DRAM_BYTES_PER_CELL = 292.6
 FP64_LANE_OPS_PER_SM_CLK = 2

@@ -26,7 +26,7 @@
  * fusion or reordering.  Build with -ffp-contract=off so that no fused
  * multiply-add changes rounding between machines.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  R1  D3Q19 order: 0 rest; 1..6 axis (+x,-x,+y,-y,+z,-z); 7..18 diagonals
  *      in opposite pairs; weights 1/3, 1/18, 1/36 (Sec. 2.1 "as in Qian").
  *  R2  Forcing Eq. (7) is applied unsplit, without a (1 - 1/2tau) factor;

@@ -15,7 +15,7 @@ rho0 u_ref^2 D^3) are directly comparable.
    fine steps of that coarse step) - (coarse force).
 3. Training: full-batch Adam on the GPU with the library's kernels.
 4. Evaluation: free coarse runs with and without the correction against the
-   fine run's settling velocity (the plain fine solver is the judge).
+   fine run's settling velocity (the plain fine solver is the reference).
 
 Every numerical step runs in the CUDA library; this module moves arrays and
 calls the C ABI.  PyTorch provides the device buffers.
