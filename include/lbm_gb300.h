@@ -241,7 +241,8 @@ int lbm_abi_version(void);
  * fixed-order force/torque total of that sweep -- but no subcycle average,
  * rigid-body update or MEM refilling, and no handle.
  *   cfg              configuration as for lbm_create; storage must be
- *                    LBM_STORE_F64 (LBM_ERR_UNSUPPORTED otherwise).
+ *                    LBM_STORE_F64 (LBM_ERR_UNSUPPORTED otherwise); LBM_MEM_MR
+ *                    is refused as in lbm_create (|Lambda_- - 1/2| < 0.01).
  *   src_pdf_dev      device, 19*N doubles: post-collision PDFs (the layout
  *                    of lbm_get_fields(LBM_FIELD_PDF)); read only.
  *   dst_pdf_dev      device, 19*N doubles, distinct from src: receives the
