@@ -6,6 +6,8 @@ invariances, brute force on tiny inputs, and values printed in the paper.
 A plausible mistake anywhere in the oracle (a dropped term, a wrong sign, a
 swapped index, a transposed operand) breaks at least one of them.
 """
+import functools
+
 import numpy as np
 import pytest
 import scipy.sparse
@@ -425,6 +427,7 @@ def test_mr_coefficients_follow_from_the_symbolic_derivation():
 
 
 # ---- Fig. 1: drag on a simple-cubic sphere array in Stokes flow ------------------------------
+@functools.lru_cache(maxsize=None)
 def _drag_coefficient(coupling, tau, tol=2e-6):
     """C of Sec. 3 (Eq. (30), (31)) on the paper's set-up: L = 32, D = 16,
     a = 1e-5, run until C changes by less than `tol` (relative) per 250 steps."""
@@ -470,6 +473,20 @@ def test_fig1_drag_error(coupling):
     C = _drag_coefficient(coupling, tau)
     err = (C / 2.8402 - 1.0) * 100.0
     assert abs(err - ref) < 0.3, (coupling, err, ref)
+
+
+@pytest.mark.slow
+def test_fig1_mr_is_viscosity_independent():
+    """MR's correction term carries the Lambda_- dependence (R17): at tau = 1.5
+    (Lambda_- = 3/16) its scale differs from tau = 1.0 (Lambda_- = 3/8) by a
+    factor ~1.7, yet the drag error must stay on the paper's flat MR curve
+    (Fig. 1: +0.25 % at both) and within 0.05 points of the tau = 1.0 value."""
+    ref = _fig1_reference()
+    errs = {}
+    for tau in (1.0, 1.5):
+        errs[tau] = (_drag_coefficient("MEM_MR", tau) / 2.8402 - 1.0) * 100.0
+        assert abs(errs[tau] - ref[("MEM_MR", tau)]) < 0.3, (tau, errs[tau])
+    assert abs(errs[1.5] - errs[1.0]) < 0.05, errs
 
 
 # ---- open z boundaries of the benchmark frame (Sec. 4.1) -----------------------------
