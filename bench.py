@@ -238,7 +238,9 @@ def run_learned(args, stream):
 
 
 def run_frame_study(args):
-    """Case A of the paper's benchmark frame (Sec. 4.1) at diameter --frame."""
+    """The paper's benchmark frame (Sec. 4.1) at diameter --frame: case A
+    (Ga = 144, compared with Tab. 1) unless --frame-ga / --frame-upv-ref name
+    another Galileo number and its reference u_pV."""
     import torch
 
     from paper_1702_04910_gb300 import frame
@@ -256,15 +258,17 @@ def run_frame_study(args):
     out = {}
     for coupling in args.frame_couplings:
         t0 = time.perf_counter()
-        r = frame.run_frame(D=args.frame, coupling=coupling, storage="f64fx", stream=stream)
-        paper = table.get((coupling, int(round(args.frame))))
+        r = frame.run_frame(D=args.frame, ga_target=args.frame_ga, u_pv_ref=args.frame_upv_ref,
+                            coupling=coupling, storage=args.frame_storage, stream=stream)
+        paper = table.get((coupling, int(round(args.frame)))) if args.frame_ga == 144.0 else None
         out[coupling] = {"u_pV": r["u_pV"], "u_pV_paper_tab1": paper,
                          "rel_diff_vs_paper": (abs(r["u_pV"] - paper) / abs(paper)) if paper else None,
                          "Ga": r["calibration"][-1]["Ga"], "nu": r["nu"],
                          "calibration_steps": r["calibration_steps"], "free_steps": r["free_steps"],
                          "seconds": time.perf_counter() - t0}
-    print(json.dumps({"frame": "case A, Ga = 144", "D": args.frame, "shape": frame.frame_shape(args.frame),
-                      "results": out}), flush=True)
+    print(json.dumps({"frame": f"Ga = {args.frame_ga:g}, reference u_pV {args.frame_upv_ref:g}",
+                      "D": args.frame, "storage": args.frame_storage,
+                      "shape": frame.frame_shape(args.frame), "results": out}), flush=True)
 
 
 def run_ensemble_only(args):
@@ -631,6 +635,12 @@ def main():
     ap.add_argument("--frame", type=float, default=None, metavar="D",
                     help="run the paper's benchmark frame (case A, Ga = 144) at diameter D for "
                          "MEM BB/CLI/MR and PSM M1B1/M2B2 and print u_pV against the paper's Tab. 1")
+    ap.add_argument("--frame-ga", type=float, default=144.0,
+                    help="Galileo number of the frame study (144: case A, compared with Tab. 1)")
+    ap.add_argument("--frame-upv-ref", type=float, default=-1.285,
+                    help="reference u_pV that sets the inflow Reynolds number |u_pV| Ga")
+    ap.add_argument("--frame-storage", default="f64fx",
+                    choices=("f64", "f64fx", "f64ff", "f32", "f16s", "bf16s"))
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the settling workload by this factor in every length (tests)")
     ap.add_argument("--case-shape", default=None,
