@@ -806,6 +806,17 @@ int orc_set_particles(orc_sim *s, int np, const orc_particle *parts) {
     return ORC_OK;
 }
 
+/* Re-mapping and PDF reconstruction of Sec. 2.2 on its own, for the pins:
+ * the particles take the given state (as after a rigid-body update) and
+ * every cell they uncover is rebuilt from the current pre-collision field by
+ * the same routine the MEM global step calls after its rigid-body update. */
+int orc_move_and_refill(orc_sim *s, int np, const orc_particle *parts) {
+    if (!is_mem(s->p.coupling) || !s->mapped || np != s->np) return ORC_ERR_ARG;
+    if (np) memcpy(s->part, parts, sizeof(orc_particle) * (size_t)np);
+    remap_and_refill(s, 1);
+    return ORC_OK;
+}
+
 int orc_get_particles(const orc_sim *s, orc_particle *out) {
     if (s->np) memcpy(out, s->part, sizeof(orc_particle) * (size_t)s->np);
     return s->np;

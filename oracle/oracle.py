@@ -76,6 +76,7 @@ def _load():
         lib.orc_destroy.argtypes = [P]
         lib.orc_set_particles.argtypes = [P, ct.c_int, ct.POINTER(Particle)]
         lib.orc_get_particles.argtypes = [P, ct.POINTER(Particle)]
+        lib.orc_move_and_refill.argtypes = [P, ct.c_int, ct.POINTER(Particle)]
         lib.orc_init_equilibrium.argtypes = [P, ct.c_double, dp]
         lib.orc_set_pdf.argtypes = [P, dp]
         lib.orc_step.argtypes = [P, ct.c_int]
@@ -179,8 +180,8 @@ class Oracle:
     def lambda_minus(self):
         return self._lib.orc_lambda_minus(self._h)
 
-    def set_particles(self, particles):
-        """particles: list of dicts with x, u, omega, diameter, density, fixed."""
+    @staticmethod
+    def _records(particles):
         arr = (Particle * max(1, len(particles)))()
         for i, d in enumerate(particles):
             for a in range(3):
@@ -190,10 +191,23 @@ class Oracle:
             arr[i].diameter = float(d["diameter"])
             arr[i].density = float(d.get("density", 1.0))
             arr[i].fixed = int(d.get("fixed", 0))
+        return arr
+
+    def set_particles(self, particles):
+        """particles: list of dicts with x, u, omega, diameter, density, fixed."""
+        arr = self._records(particles)
         st = self._lib.orc_set_particles(self._h, len(particles), arr)
         if st != 0:
             raise ValueError(f"oracle set_particles failed ({st})")
         self.np = len(particles)
+
+    def move_and_refill(self, particles):
+        """MEM only: give the mapped particles a new state (as a rigid-body
+        update would) and run the re-mapping and PDF reconstruction of
+        Sec. 2.2 alone on the current pre-collision field."""
+        st = self._lib.orc_move_and_refill(self._h, len(particles), self._records(particles))
+        if st != 0:
+            raise ValueError(f"oracle move_and_refill failed ({st})")
 
     def get_particles(self):
         arr = (Particle * max(1, self.np))()
