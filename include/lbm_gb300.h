@@ -52,7 +52,8 @@ typedef enum {
     LBM_ERR_CUDA = -2,        /* a CUDA runtime call failed                       */
     LBM_ERR_OOM = -3,         /* device or pinned host allocation failed          */
     LBM_ERR_UNSTABLE = -4,    /* a particle state became non-finite or moved a    */
-                              /* cell or more per step (update not applied)       */
+                              /* cell or more per step (update not applied), or a */
+                              /* fluid cell's density became non-finite or <= 0   */
     LBM_ERR_DOMAIN = -5,      /* a particle left the domain through a closed wall */
     LBM_ERR_TIMEOUT = -6,     /* reserved: a bounded device wait gave up          */
     LBM_ERR_UNSUPPORTED = -7  /* configuration not implemented (e.g. MR near |lambda_-| = 1) */
@@ -126,7 +127,8 @@ typedef struct {
     double gravity[3];         /* acceleration acting on the particles            */
     double rho0;               /* reference density rho_0 (> 0)                   */
     int subsample;             /* PSM: n of the n^3 supersampling (0 -> 4)        */
-    int lbm_subcycles;         /* LBM sweeps per global step (0 -> 2 MEM, 1 PSM)  */
+    int lbm_subcycles;         /* LBM sweeps per global step, forces averaged over */
+                               /* them (0 -> 2 MEM, 1 PSM; PSM 2: Sec. 4.1)      */
     int wall_contact;          /* 1: keep spheres one cell off closed z walls     */
     int storage;               /* lbm_storage                                     */
     double inflow[3];          /* bc_z = 2: inflow velocity at z = 0              */
@@ -179,12 +181,14 @@ lbm_status lbm_get_particles(lbm_handle *h, lbm_particle *host_out);
 lbm_status lbm_init_equilibrium(lbm_handle *h, double rho, const double u[3]);
 
 /* Advance nsteps global time steps (Algorithm 1 for MEM, Algorithm 2 for
- * PSM; MEM runs lbm_subcycles LBM sweeps per step).  Asynchronous: returns
- * after enqueueing. */
+ * PSM).  Each step runs lbm_subcycles LBM sweeps with the particle state of
+ * its start (MEM default 2; PSM default 1, or 2 as in the settling benchmark
+ * of Sec. 4.1), averages their forces and advances the particles by
+ * dt = lbm_subcycles.  Asynchronous: returns after enqueueing. */
 lbm_status lbm_step(lbm_handle *h, int nsteps);
 
 /* Hydrodynamic force and torque of the last global step, Eq. (17)-(18)
- * (MEM, averaged over the subcycles) or Eq. (28)-(29) (PSM).  F and T are
+ * (MEM) or Eq. (28)-(29) (PSM), averaged over the step's subcycles.  F and T are
  * host arrays of 3*n doubles [particle][3].  Synchronises and reports any
  * device status raised since the last synchronising call. */
 lbm_status lbm_get_forces(lbm_handle *h, double *F, double *T);
@@ -222,8 +226,29 @@ void lbm_destroy(lbm_handle *h);
  * static string for h == NULL). */
 const char *lbm_last_error(const lbm_handle *h);
 
+/* Measurement utility; the paper has no counterpart.  The FP64 sweep is
+ * bound by the rate at which the GPU issues FP64 instructions, so its
+ * roofline needs that rate measured on the device.  Runs independent chains
+ * of FP64 fused multiply-adds on every SM of the current device (stream: a
+ * cudaStream_t or NULL), times them with CUDA events (best of three launches
+ * after a warm-up, a few milliseconds in all) and stores the DFMA
+ * lane-operations per second in *dfma_per_second (one DFMA = 2 flops).
+ * Synchronises the stream.  LBM_ERR_ARG for a NULL output, LBM_ERR_CUDA when
+ * a CUDA call fails (the output is then 0). */
+lbm_status lbm_measure_fp64_rate(void *stream, double *dfma_per_second);
+
 /* ABI version of this header: 1. */
 int lbm_abi_version(void);
+
+/* Bits the kernels OR into a device status word (lbm_sweep_noalloc's
+ * status_dev; the handle and the batch map them to return codes). */
+enum {
+    LBM_STATUS_TOO_MANY_OBJECTS = 1, /* more than two particles touch one cell          */
+    LBM_STATUS_DOMAIN = 2,           /* a particle left through a closed wall           */
+    LBM_STATUS_UNSTABLE = 8,         /* a particle state became non-finite or too fast  */
+    LBM_STATUS_BOUNDS = 16,          /* an index check in a coupling kernel failed      */
+    LBM_STATUS_FLUID = 32            /* a fluid cell's density became non-finite or <= 0 */
+};
 
 /* Capacity, in doubles, of the fixed force-partial scratch that
  * lbm_sweep_noalloc uses: 524288 doubles = 4 MiB per GPU. */
@@ -250,11 +275,17 @@ int lbm_abi_version(void);
  *                    they were).
  *   n, particles_host   0..32 particle records on the host (copied).
  *   force_torque_dev device, 6*n doubles [particle][Fx,Fy,Fz,Tx,Ty,Tz].
- *   status_dev       device int or NULL; kernels OR status bits into it
- *                    (the caller zeroes it); NULL uses an internal word.
+ *   status_dev       device int or NULL; kernels OR LBM_STATUS_* bits into
+ *                    it (the caller zeroes it and reads it after the work
+ *                    has finished).  NULL sends the bits to an internal word
+ *                    that the caller cannot read, so device-side errors of
+ *                    the call (an index check, more than two objects in a
+ *                    cell, a fluid cell whose density became non-finite or
+ *                    <= 0) are then discarded.
  *   stream           cudaStream_t or NULL; work is enqueued there and the
- *                    call returns after enqueueing (it waits only for the
- *                    particle upload).
+ *                    call returns after enqueueing.  It waits for nothing:
+ *                    the particle records reach the device as a kernel
+ *                    argument.
  *   err, err_len     optional buffer for a message on failure.
  * Scratch: the force partials of the near-particle blocks live in a fixed
  * device array of LBM_NOALLOC_MAX_PARTIAL_DOUBLES doubles, next to a
@@ -293,7 +324,7 @@ lbm_status lbm_sweep_noalloc(const lbm_config *cfg, const double *src_pdf_dev,
  *     timing them (results do not depend on the choice).
  * Each case follows the step contract of lbm_step (MEM: lbm_subcycles
  * sweeps, averaged forces, rigid-body update with dt = subcycles, refilling;
- * PSM: one sweep, dt = 1).  The stored state of every case starts as the
+ * PSM: lbm_subcycles sweeps, default one).  The stored state of every case starts as the
  * fluid at rest, f~ = f_eq(rho0, 0) (Eq. (3)), taken as the post-collision
  * field of step 0. */
 typedef struct lbm_batch lbm_batch;
@@ -413,7 +444,9 @@ lbm_status lbm_mlp_set_normalization(lbm_mlp *m, const float *host, size_t count
 lbm_status lbm_mlp_get_normalization(lbm_mlp *m, float *host, size_t count);
 
 /* Fits the normalisation to n samples on the device: mu and 1/sigma per input
- * (sigma < 1e-6 -> 1), s_out = RMS of each target (floored at 1e-12).
+ * (sigma < 1e-6 -> 1); s_out = one RMS over the three force targets and one
+ * over the three torque targets (floored at 1e-12), so each component keeps
+ * its physical size in the loss.
  * x_dev: n x LBM_MLP_IN floats; t_dev: n x LBM_MLP_OUT floats. */
 lbm_status lbm_mlp_fit_normalization(lbm_mlp *m, const float *x_dev, const float *t_dev, int n);
 

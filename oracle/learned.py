@@ -98,14 +98,20 @@ def adam(P, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def fit_normalization(X, T):
-    """mu and 1/sigma per input (sigma < 1e-6 -> 1); RMS per target (>= 1e-12)."""
+    """mu and 1/sigma per input (sigma < 1e-6 -> 1).  Output scale: one RMS
+    for the three force components together and one for the three torque
+    components (>= 1e-12), so that the loss weighs each component by its
+    physical size -- a per-component RMS would blow near-zero lateral targets
+    up to the size of the drag correction."""
     X = np.asarray(X, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
     mu = X.mean(axis=0)
     sd = np.sqrt(((X - mu) ** 2).mean(axis=0))
     inv = np.where(sd > 1e-6, 1.0 / np.where(sd > 1e-6, sd, 1.0), 1.0)
-    rms = np.sqrt((T * T).mean(axis=0))
-    return np.concatenate([mu, inv, np.maximum(rms, 1e-12)])
+    rms_f = np.sqrt((T[:, :3] * T[:, :3]).mean())
+    rms_t = np.sqrt((T[:, 3:] * T[:, 3:]).mean())
+    s = np.array([rms_f] * 3 + [rms_t] * 3)
+    return np.concatenate([mu, inv, np.maximum(s, 1e-12)])
 
 
 # ---- feature stencil ----------------------------------------------------------------

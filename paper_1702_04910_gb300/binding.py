@@ -25,6 +25,9 @@ LBM_ERR_UNSTABLE, LBM_ERR_DOMAIN, LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED = -4, -5,
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
                 -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_DOMAIN", -6: "LBM_ERR_TIMEOUT",
                 -7: "LBM_ERR_UNSUPPORTED"}
+# bits kernels OR into a device status word (lbm_sweep_noalloc's status_dev)
+STATUS_BITS = {"LBM_STATUS_TOO_MANY_OBJECTS": 1, "LBM_STATUS_DOMAIN": 2, "LBM_STATUS_UNSTABLE": 8,
+               "LBM_STATUS_BOUNDS": 16, "LBM_STATUS_FLUID": 32}
 
 COUPLING = {"PSM_M1B1": 0, "PSM_M2B2": 1, "PSM_M3B2": 2, "MEM_BB": 3, "MEM_CLI": 4,
             "MEM_MR": 5, "NONE": 6}
@@ -44,7 +47,7 @@ EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_eq
             "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_last_error", "lbm_mlp_set_params",
             "lbm_mlp_get_params", "lbm_mlp_set_normalization", "lbm_mlp_get_normalization",
             "lbm_mlp_fit_normalization", "lbm_mlp_forward", "lbm_mlp_gradient", "lbm_mlp_train",
-            "lbm_set_force_model", "lbm_get_features")
+            "lbm_set_force_model", "lbm_get_features", "lbm_measure_fp64_rate")
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS, MLP_NORM = 512, 64, 6, 37382, 1030
 BATCH_LAYOUTS = {"box32": 0, "box64": 1, "box128": 2, "plane": 3}
 
@@ -136,6 +139,7 @@ def load(build_if_missing: bool = True):
             "lbm_mlp_train": (i, [vp, vp, vp, i, i, ct.c_float, dp]),
             "lbm_set_force_model": (i, [vp, vp, ct.c_double, i]),
             "lbm_get_features": (i, [vp, fp, sz]),
+            "lbm_measure_fp64_rate": (i, [vp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -429,6 +433,16 @@ def lbm_get_features(h, n: int) -> np.ndarray:
     a = np.empty((n, MLP_IN), dtype=np.float32)
     _check(h, load().lbm_get_features(h, _fptr(a), a.size))
     return a
+
+
+def lbm_measure_fp64_rate(stream: int | None = None) -> float:
+    """Measured FP64 fused multiply-add lane-operations per second of the
+    current device (the FP64 roofline of the sweep)."""
+    out = ct.c_double(0.0)
+    st = load().lbm_measure_fp64_rate(ct.c_void_p(stream or 0), ct.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, "FP64 rate probe failed")
+    return out.value
 
 
 # ---- convenience wrapper ------------------------------------------------------------

@@ -2,8 +2,9 @@
 // include/lbm_gb300.h).  Host orchestration of one global step:
 //
 //   PSM (Algorithm 2 of Rettinger & Ruede, arXiv:1702.04910):
-//     bulk + near sweep (solid fractions, weighted collision, force partials)
-//     -> force total -> rigid-body update (dt = 1)
+//     lbm_subcycles (default 1) x bulk + near sweep (solid fractions,
+//     weighted collision, force partials) -> averaged force total ->
+//     rigid-body update (dt = number of subcycles)
 //   MEM (Algorithm 1):
 //     lbm_subcycles x (bulk + near sweep with link boundary conditions and
 //     link-force partials) -> averaged force total -> rigid-body update
@@ -18,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/lbm_gb300.h"
@@ -274,7 +276,7 @@ lbm_status sweep(lbm_handle* h, int sub, bool with_map) {
 lbm_status step_once(lbm_handle* h) {
     lbm_status st;
     const int coupled = h->np > 0 && h->kind != 0;
-    const int nsub = h->kind == 2 ? h->subcycles : 1;
+    const int nsub = h->kind != 0 ? h->subcycles : 1;
     // the geometry of the current particle state, shared by the step's
     // sweeps, is built by the first sweep (side stream)
     for (int s = 0; s < nsub; ++s)
@@ -326,14 +328,24 @@ lbm_status read_status(lbm_handle* h) {
     std::memcpy(&st, &h->h_stage[0], sizeof(int));
     if (st) {
         CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream), "status reset");
-        if (st & ST_DOMAIN) return fail(h, LBM_ERR_DOMAIN, "a particle left the domain through a closed wall");
-        if (st & ST_BOUNDS)
-            return fail(h, LBM_ERR_CUDA, "an index check in a coupling kernel failed; the step is invalid");
-        if (st & ST_UNSTABLE)
-            return fail(h, LBM_ERR_UNSTABLE,
-                        "a particle state became non-finite or moved a cell or more per step");
-        if (st & ST_TOO_MANY_OBJECTS)
-            return fail(h, LBM_ERR_UNSUPPORTED, "more than two particles touch one cell");
+        // every raised condition is named; the return code follows the first
+        // of: domain, index check, instability (particle or fluid), objects
+        std::string msg;
+        const auto add = [&msg](const char* m) {
+            if (!msg.empty()) msg += "; ";
+            msg += m;
+        };
+        if (st & ST_DOMAIN) add("a particle left the domain through a closed wall");
+        if (st & ST_BOUNDS) add("an index check in a coupling kernel failed; the step is invalid");
+        if (st & ST_FLUID) add("a fluid cell's density became non-finite or <= 0 (the flow is unstable)");
+        if (st & ST_UNSTABLE) add("a particle state became non-finite or moved a cell or more per step");
+        if (st & ST_TOO_MANY_OBJECTS) add("more than two particles touch one cell");
+        const lbm_status code = (st & ST_DOMAIN)                  ? LBM_ERR_DOMAIN
+                                : (st & ST_BOUNDS)                ? LBM_ERR_CUDA
+                                : (st & (ST_FLUID | ST_UNSTABLE)) ? LBM_ERR_UNSTABLE
+                                : (st & ST_TOO_MANY_OBJECTS)      ? LBM_ERR_UNSUPPORTED
+                                                                  : LBM_ERR_CUDA;
+        if (!msg.empty()) return fail(h, code, msg.c_str());
         return fail(h, LBM_ERR_CUDA, "device status raised");
     }
     return LBM_OK;
@@ -359,27 +371,11 @@ size_t lbm_device_bytes(const lbm_handle* h) {
 lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     if (!cfg || !out) return LBM_ERR_ARG;
     *out = nullptr;
-    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return LBM_ERR_ARG;
-    if (!(cfg->tau > 0.5) || !(cfg->rho0 > 0.0) || !std::isfinite(cfg->tau)) return LBM_ERR_ARG;
-    if (cfg->coupling < 0 || cfg->coupling > LBM_NONE) return LBM_ERR_ARG;
-    if (cfg->collision != LBM_BGK && cfg->collision != LBM_TRT) return LBM_ERR_ARG;
-    if (cfg->storage < LBM_STORE_F64 || cfg->storage > LBM_STORE_BF16S) return LBM_ERR_ARG;
-    if (cfg->bc_z < 0 || cfg->bc_z > 2 || (cfg->bc_z == 2 && cfg->nz < 3)) return LBM_ERR_ARG;
-    if (cfg->bc_z == 2 &&
-        !(std::isfinite(cfg->inflow[0]) && std::isfinite(cfg->inflow[1]) && std::isfinite(cfg->inflow[2]) &&
-          cfg->rho_out > 0.0 && std::isfinite(cfg->rho_out)))
-        return LBM_ERR_ARG;
-    if (cfg->subsample < 0 || cfg->subsample > 40 || cfg->lbm_subcycles < 0) return LBM_ERR_ARG;
-    if (cfg->coupling == LBM_MEM_MR && !mr_supported(*cfg)) return LBM_ERR_UNSUPPORTED;
-    if (cfg->collision == LBM_TRT) {
-        double lp = -1.0 / cfg->tau;
-        double denom = cfg->magic / (0.5 + 1.0 / lp) - 0.5;
-        if (!(cfg->magic > 0.0) || denom == 0.0) return LBM_ERR_ARG;
-        double lm = 1.0 / denom;
-        if (!(lm > -2.0 && lm < 0.0)) return LBM_ERR_ARG;
+    {
+        const lbm_status st = check_config(*cfg);
+        if (st != LBM_OK) return st;
     }
     const long long n = (long long)cfg->nx * cfg->ny * cfg->nz;
-    if (n > (1LL << 40)) return LBM_ERR_ARG;
 
     lbm_handle* h = new (std::nothrow) lbm_handle();
     if (!h) return LBM_ERR_OOM;
@@ -412,8 +408,10 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
     h->kind = is_psm(cfg->coupling) ? 1 : (is_mem(cfg->coupling) ? 2 : 0);
     h->variant = h->kind == 1 ? cfg->coupling - LBM_PSM_M1B1
                               : (h->kind == 2 ? cfg->coupling - LBM_MEM_BB : 0);
+    // MEM: 2 sweeps by default (Algorithm 1); PSM: 1 (Algorithm 2), or the
+    // two averaged subcycles of the settling benchmark of Sec. 4.1 on request
     h->subcycles = cfg->lbm_subcycles > 0 ? cfg->lbm_subcycles : (h->kind == 2 ? 2 : 1);
-    if (h->kind != 2) h->subcycles = 1;
+    if (h->kind == 0) h->subcycles = 1;
 
     Geom& g = h->g;
     g.nx = cfg->nx;

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/lbm_gb300.h"
@@ -201,7 +202,7 @@ cudaError_t enqueue_step(lbm_batch* b, int* kernels) {
         }
         if (e == cudaSuccess) e = launch_batch_near(b->dcases, nl.view(), nl.total, sub, b->dstatus, b->side);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
-        if (e == cudaSuccess) e = launch_batch_bulk(b->mode, b->dcases, bl.view(), bl.total, b->grid, s);
+        if (e == cudaSuccess) e = launch_batch_bulk(b->mode, b->dcases, bl.view(), bl.total, b->grid, b->dstatus, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
         if (e == cudaSuccess) e = launch_batch_swap(b->dcases, nl.view(), s);
         k += 3;
@@ -243,13 +244,24 @@ lbm_status read_status(lbm_batch* b) {
     BK(b, cudaStreamSynchronize(b->stream), "stream synchronize");
     if (st) {
         BK(b, cudaMemsetAsync(b->dstatus, 0, sizeof(int), b->stream), "status reset");
-        if (st & ST_DOMAIN) return fail(b, LBM_ERR_DOMAIN, "a particle left the domain through a closed wall");
-        if (st & ST_BOUNDS)
-            return fail(b, LBM_ERR_CUDA, "an index check in a coupling kernel failed; the step is invalid");
-        if (st & ST_UNSTABLE)
-            return fail(b, LBM_ERR_UNSTABLE,
-                        "a particle state became non-finite or moved a cell or more per step");
-        if (st & ST_TOO_MANY_OBJECTS) return fail(b, LBM_ERR_UNSUPPORTED, "more than two particles touch one cell");
+        // every raised condition is named; the return code follows the first
+        // of: domain, index check, instability (particle or fluid), objects
+        std::string msg;
+        const auto add = [&msg](const char* m) {
+            if (!msg.empty()) msg += "; ";
+            msg += m;
+        };
+        if (st & ST_DOMAIN) add("a particle left the domain through a closed wall");
+        if (st & ST_BOUNDS) add("an index check in a coupling kernel failed; the step is invalid");
+        if (st & ST_FLUID) add("a fluid cell's density became non-finite or <= 0 (the flow is unstable)");
+        if (st & ST_UNSTABLE) add("a particle state became non-finite or moved a cell or more per step");
+        if (st & ST_TOO_MANY_OBJECTS) add("more than two particles touch one cell");
+        const lbm_status code = (st & ST_DOMAIN)                  ? LBM_ERR_DOMAIN
+                                : (st & ST_BOUNDS)                ? LBM_ERR_CUDA
+                                : (st & (ST_FLUID | ST_UNSTABLE)) ? LBM_ERR_UNSTABLE
+                                : (st & ST_TOO_MANY_OBJECTS)      ? LBM_ERR_UNSUPPORTED
+                                                                  : LBM_ERR_CUDA;
+        if (!msg.empty()) return fail(b, code, msg.c_str());
         return fail(b, LBM_ERR_CUDA, "device status raised");
     }
     return LBM_OK;
@@ -309,7 +321,7 @@ lbm_status make_case(lbm_batch* b, int c, const lbm_config& cfg, const lbm_parti
     set_tiling(g, LBM_BATCH_PLANE);
     const bool psm = cfg.coupling <= LBM_PSM_M3B2;
     k.kind = psm ? 1 : 2;
-    k.subcycles = psm ? 1 : (cfg.lbm_subcycles > 0 ? cfg.lbm_subcycles : 2);
+    k.subcycles = cfg.lbm_subcycles > 0 ? cfg.lbm_subcycles : (psm ? 1 : 2);
     k.wall_contact = cfg.wall_contact ? 1 : 0;
     k.cp.kind = k.kind;
     k.cp.variant = psm ? cfg.coupling - LBM_PSM_M1B1 : cfg.coupling - LBM_MEM_BB;
@@ -367,10 +379,10 @@ void release(lbm_batch* b) {
 // the given grid.  src = buf[cur], dst = buf[1 - cur]: the next sweep
 // overwrites every cell this writes, so the simulation state is unchanged.
 lbm_status time_bulk(lbm_batch* b, const WorkList& w, int grid, int reps, double* ms) {
-    BK(b, launch_batch_bulk(b->mode, b->dcases, w.view(), w.total, grid, b->stream), "tuning launch");
+    BK(b, launch_batch_bulk(b->mode, b->dcases, w.view(), w.total, grid, b->dstatus, b->stream), "tuning launch");
     BK(b, cudaEventRecord(b->t0, b->stream), "event record");
     for (int r = 0; r < reps; ++r)
-        BK(b, launch_batch_bulk(b->mode, b->dcases, w.view(), w.total, grid, b->stream),
+        BK(b, launch_batch_bulk(b->mode, b->dcases, w.view(), w.total, grid, b->dstatus, b->stream),
            "tuning launch");
     BK(b, cudaEventRecord(b->t1, b->stream), "event record");
     BK(b, cudaEventSynchronize(b->t1), "event sync");

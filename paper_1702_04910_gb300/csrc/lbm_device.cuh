@@ -233,6 +233,12 @@ __device__ __forceinline__ bool in_range(int i, int lo, int len, int n) {
     return range_off(i, lo, n) < len;
 }
 
+// Whether the cell ranges [a, a + la) and [r, r + lr) of a periodic axis of
+// n cells share a cell (a, r in [0, n); la, lr >= 1).
+__device__ __forceinline__ bool spans_meet(int a, int la, int r, int lr, int n) {
+    return range_off(a, r, n) < lr || range_off(r, a, n) < la;
+}
+
 struct NearRegion {
     AxisRange ax[3];
 };
@@ -553,10 +559,30 @@ __device__ __forceinline__ void trt_pair_sd(C (&f)[NQ], C cu, C P, const Coll<C>
     f[QB] = (sp - sd) - (P - M);
 }
 
-template <typename C, bool FORCE>
-__device__ __forceinline__ void collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
+// Fluid health: the density of Eq. (4) of a cell must be finite and
+// positive.  Bit tests on the integer pipes (no FP64 instruction): a value
+// outside (0, +inf) -- zero, negative, infinite or NaN -- is reported.  (The
+// float-float form is in lbm_dfloat.cuh; overloads are found at
+// instantiation.)
+__device__ __forceinline__ bool density_bad(double r) {
+    return (unsigned long long)__double_as_longlong(r) - 1ull >= 0x7FEFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ bool density_bad(float r) {
+    return __float_as_uint(r) - 1u >= 0x7F7FFFFFu;
+}
+// fixed point cannot hold NaN; a saturated conversion or a wrapped sum shows
+// as a density outside (0, 16)
+__device__ __forceinline__ bool density_bad(fx64 r) {
+    return !(r.v > 0 && r.v < (16LL << FX_SHIFT));
+}
+
+// Returns true when the cell's density is not finite and positive.
+// SHIFTED: f holds the shifted populations f_q - w_q, whose sum is rho - 1.
+template <typename C, bool FORCE, bool SHIFTED>
+__device__ __forceinline__ bool collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
     C rho, ux, uy, uz;
     moments(f, k, rho, ux, uy, uz);
+    const bool bad = SHIFTED ? density_bad(rho + (C)1) : density_bad(rho);
     if constexpr (PairSumDiff<C>::value && !FORCE) {
         // products shared between pairs: with t_a = k1w_diag u_a^2 and
         // c_ab = k1w_axis u_a u_b (k1w_axis = 2 k1w_diag), the quadratic term
@@ -578,7 +604,7 @@ __device__ __forceinline__ void collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
         trt_pair_sd<C, 13, 2>(f, ux - uz, ((tx + tz) - cxz) + bw[2], k);
         trt_pair_sd<C, 15, 2>(f, uy + uz, ((ty + tz) + cyz) + bw[2], k);
         trt_pair_sd<C, 17, 2>(f, uy - uz, ((ty + tz) - cyz) + bw[2], k);
-        return;
+        return bad;
     }
     const C uu = fma(ux, ux, fma(uy, uy, uz * uz));
     const C base = fma(k.m15r0, uu, rho);
@@ -601,16 +627,17 @@ __device__ __forceinline__ void collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
     trt_pair<C, 13, 2, FORCE>(f, ux - uz, bw, k);
     trt_pair<C, 15, 2, FORCE>(f, uy + uz, bw, k);
     trt_pair<C, 17, 2, FORCE>(f, uy - uz, bw, k);
+    return bad;
 }
 
 // Fluid collision Eq. (1) with TRT Eq. (9)-(10) (BGK: lambda_- = lambda_+)
-// and forcing Eq. (7), in place.
-template <typename C>
-__device__ __forceinline__ void collide_fluid(C (&f)[NQ], const Coll<C>& k) {
-    if (k.has_force)
-        collide_fluid_t<C, true>(f, k);
-    else
-        collide_fluid_t<C, false>(f, k);
+// and forcing Eq. (7), in place.  Returns true when the cell's density is
+// not finite and positive (density_bad).  SHIFTED: f holds f_q - w_q (the
+// 16-bit storage's populations, collided as they are).
+template <typename C, bool SHIFTED = false>
+__device__ __forceinline__ bool collide_fluid(C (&f)[NQ], const Coll<C>& k) {
+    if (k.has_force) return collide_fluid_t<C, true, SHIFTED>(f, k);
+    return collide_fluid_t<C, false, SHIFTED>(f, k);
 }
 
 // Collision operator values C_q (Eq. (5)/(9)) and forcing F_q (Eq. (7)) as

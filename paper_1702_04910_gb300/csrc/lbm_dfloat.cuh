@@ -135,4 +135,10 @@ __device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) {
 
 __device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
 
+// Fluid health test of a float-float density (see density_bad in
+// lbm_device.cuh): the head decides.
+__device__ __forceinline__ bool density_bad(dfloat r) {
+    return __float_as_uint(r.hi) - 1u >= 0x7F7FFFFFu;
+}
+
 }  // namespace lbmgpu

@@ -428,9 +428,10 @@ __device__ __forceinline__ void mem_links_warp(const T* __restrict__ src, const 
 // ---------------------------------------------------------------------------
 // PSM weighted collision Eq. (26) with C^PSM Eq. (20), B1/B2 Eq. (21)/(22),
 // M1/M2/M3 Eq. (23)-(25), force/torque Eq. (28)-(29).  `eps[k]` are the
-// solid fractions of particles `pid[k]` (k < nobj) at this cell.
+// solid fractions of particles `pid[k]` (k < nobj) at this cell.  Returns
+// true when the cell's fluid density is not finite and positive.
 template <typename C>
-__device__ inline void psm_collide(C (&f)[NQ], const Coll<C>& k, const Coupl& cp, const Geom& g,
+__device__ inline bool psm_collide(C (&f)[NQ], const Coll<C>& k, const Coupl& cp, const Geom& g,
                                    const DevParticle* parts, int nobj, const int (&pid)[CELL_SLOTS],
                                    const double (&eps)[CELL_SLOTS], int x, int y, int z,
                                    Slots& slots) {
@@ -478,6 +479,7 @@ __device__ inline void psm_collide(C (&f)[NQ], const Coll<C>& k, const Coupl& cp
     const C oneB = (C)(1.0 - B);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) f[q] = f[q] + (oneB * Cf[q] + ssum[q]) + oneB * Fq[q];
+    return density_bad(rho);
 }
 
 // ---------------------------------------------------------------------------
@@ -492,7 +494,8 @@ template <typename T, typename C, bool NOSTREAM, int CPT>
 __device__ __forceinline__ void bulk_tile(const T* __restrict__ src, T* __restrict__ dst,
                                           const Geom& g, const Coll<C>& k,
                                           const DevParticle* __restrict__ parts, int np,
-                                          int all_tiles, int tX, int tY, int tZ, int tx, int ty) {
+                                          int all_tiles, int tX, int tY, int tZ, int tx, int ty,
+                                          int* __restrict__ status) {
     bool near_tile = false;
     if (!all_tiles) {
         for (int s = 0; s < np && !near_tile; ++s)
@@ -519,21 +522,23 @@ __device__ __forceinline__ void bulk_tile(const T* __restrict__ src, T* __restri
                 pull_plain(src, g, x, y, z, idx, f[c]);
         }
     }
+    bool bad = false;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
         if (!act[c]) continue;
         const int z = tZ * CPT + c;
-        collide_fluid(f[c], k);
+        bad |= collide_fluid(f[c], k);
         store_own(dst, g, lin(g, x, y, z), f[c]);
     }
+    if (bad) atomicOr(status, ST_FLUID);
 }
 
 template <typename T, typename C, bool NOSTREAM, int CPT>
 __global__ void __launch_bounds__(256, BulkBlocks<C>::value)
     k_bulk(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<C> k,
-           const DevParticle* __restrict__ parts, int np, int all_tiles) {
+           const DevParticle* __restrict__ parts, int np, int all_tiles, int* __restrict__ status) {
     bulk_tile<T, C, NOSTREAM, CPT>(src, dst, g, k, parts, np, all_tiles, blockIdx.x, blockIdx.y,
-                                   blockIdx.z, threadIdx.x, threadIdx.y);
+                                   blockIdx.z, threadIdx.x, threadIdx.y, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,14 +639,22 @@ constexpr int PAIR_TX = 64, PAIR_TY = 4;
 template <typename T>
 __global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
     k_bulk_pair(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<float> k,
-                const DevParticle* __restrict__ parts, int np) {
-    const int x0 = 2 * (blockIdx.x * PAIR_TX + threadIdx.x);
-    const int y = blockIdx.y * PAIR_TY + threadIdx.y, z = blockIdx.z;
+                const DevParticle* __restrict__ parts, int np, int* __restrict__ status) {
+    const int bx0 = 2 * blockIdx.x * PAIR_TX, by0 = blockIdx.y * PAIR_TY;
+    const int x0 = bx0 + 2 * threadIdx.x;
+    const int y = by0 + threadIdx.y, z = blockIdx.z;
     if (x0 >= g.nx || y >= g.ny) return;
-    bool near_a = false, near_b = false;  // k_near's cells are left alone
+    // k_near's cells are left alone; a block whose cells no region reaches
+    // (block-uniform test) skips the per-cell one
+    bool near_a = false, near_b = false;
     for (int s = 0; s < np; ++s) {
-        near_a = near_a || cell_in_reg(g, parts[s].reg, x0, y, z);
-        near_b = near_b || cell_in_reg(g, parts[s].reg, x0 + 1, y, z);
+        const int* r = parts[s].reg;
+        if (!in_range(z, r[8], r[9], g.nz) ||
+            !spans_meet(by0, min(PAIR_TY, g.ny - by0), r[4], r[5], g.ny) ||
+            !spans_meet(bx0, min(2 * PAIR_TX, g.nx - bx0), r[0], r[1], g.nx))
+            continue;
+        near_a = near_a || cell_in_reg(g, r, x0, y, z);
+        near_b = near_b || cell_in_reg(g, r, x0 + 1, y, z);
     }
     if (near_a && near_b) return;
     const NbrOff o = make_off(g, x0, y, z);
@@ -650,8 +663,8 @@ __global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
     const int xp2 = x0 + 2 == g.nx ? 0 : x0 + 2;
     float fa[NQ], fb[NQ];
     PullPair<T, 0>::run(src, g, o, row, x0, xm2, xp2, fa, fb);
-    collide_fluid(fa, k);
-    collide_fluid(fb, k);
+    const bool bad_a = collide_fluid<float, true>(fa, k), bad_b = collide_fluid<float, true>(fb, k);
+    if ((bad_a && !near_a) || (bad_b && !near_b)) atomicOr(status, ST_FLUID);
     if (!near_a && !near_b) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
@@ -725,7 +738,7 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
             // MEM with no stream (first sweep after set-up): fluid cells collide
             if (NOSTREAM && !map_at(gm, p, kx, ky, kz)) {
                 load_own(src, g, idx, f);
-                collide_fluid(f, k);
+                if (collide_fluid(f, k)) atomicOr(status, ST_FLUID);
                 store_own(dst, g, idx, f);
             }
         } else {
@@ -753,10 +766,10 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
                     }
                 }
             }
-            if (nobj == 0)
-                collide_fluid(f, k);
-            else
-                psm_collide(f, k, cp, g, sp, nobj, pid, eps, x, y, z, slots);
+            const bool bad = nobj == 0
+                                 ? collide_fluid(f, k)
+                                 : psm_collide(f, k, cp, g, sp, nobj, pid, eps, x, y, z, slots);
+            if (bad) atomicOr(status, ST_FLUID);
             store_own(dst, g, idx, f);
         }
     }
@@ -781,7 +794,7 @@ __device__ __forceinline__ void near_block(const T* __restrict__ src, T* __restr
         mem_links_warp(src, g, cp, sp, &gm, x, y, z, idx, cut, f, slots, status, lw[tid >> 5],
                        tid & 31);
         if (fluid) {
-            collide_fluid(f, k);
+            if (collide_fluid(f, k)) atomicOr(status, ST_FLUID);
             store_own(dst, g, idx, f);
         }
     }
@@ -1460,7 +1473,7 @@ template <typename C>
 __device__ __forceinline__ void bulk_segment(const double* __restrict__ src,
                                              double* __restrict__ dst, const Geom& g,
                                              const Coll<C>& k, const int* reg, int seg, int z,
-                                             int t) {
+                                             int t, int* __restrict__ status) {
     const int l = seg * 256 + t;
     if (l >= g.nx * g.ny) return;
     const int y = l / g.nx, x = l - y * g.nx;
@@ -1468,24 +1481,26 @@ __device__ __forceinline__ void bulk_segment(const double* __restrict__ src,
     const long long idx = lin(g, x, y, z);
     C f[NQ];
     pull_plain(src, g, x, y, z, idx, f);
-    collide_fluid(f, k);
+    if (collide_fluid(f, k)) atomicOr(status, ST_FLUID);
     store_own(dst, g, idx, f);
 }
 
 // One tile of case B in its bulk layout (see k_batch_bulk).
 template <typename C>
-__device__ __forceinline__ void batch_tile(const BatchCase& B, long long local) {
+__device__ __forceinline__ void batch_tile(const BatchCase& B, long long local,
+                                           int* __restrict__ status) {
     const int cur = B.cur;
     if (B.layout == 1) {
         const int nseg = (B.g.nx * B.g.ny + 255) / 256;
         bulk_segment<C>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B), B.part->reg,
-                        (int)(local % nseg), (int)(local / nseg), threadIdx.x);
+                        (int)(local % nseg), (int)(local / nseg), threadIdx.x, status);
     } else {
         const int tX = (int)(local % B.g.ntx);
         const int tY = (int)((local / B.g.ntx) % B.g.nty);
         const int tZ = (int)(local / ((long long)B.g.ntx * B.g.nty));
         bulk_tile<double, C, false, 1>(B.buf[cur], B.buf[1 - cur], B.g, batch_coll<C>(B), B.part, 1,
-                                       0, tX, tY, tZ, threadIdx.x % B.g.tx, threadIdx.x / B.g.tx);
+                                       0, tX, tY, tZ, threadIdx.x % B.g.tx, threadIdx.x / B.g.tx,
+                                       status);
     }
 }
 
@@ -1496,13 +1511,14 @@ __device__ __forceinline__ void batch_tile(const BatchCase& B, long long local) 
 // collision.
 template <int MODE>
 __global__ void __launch_bounds__(256, 3)
-    k_batch_bulk(BatchCase* __restrict__ cases, BatchList l, long long total) {
+    k_batch_bulk(BatchCase* __restrict__ cases, BatchList l, long long total,
+                 int* __restrict__ status) {
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
         const int i = find_item(l.base, l.n, t);
         const BatchCase& B = cases[l.list[i]];
         const long long local = t - l.base[i];
-        if (MODE == 3) batch_tile<fx64>(B, local);
-        else batch_tile<double>(B, local);
+        if (MODE == 3) batch_tile<fx64>(B, local, status);
+        else batch_tile<double>(B, local, status);
     }
 }
 
@@ -1514,7 +1530,7 @@ __global__ void k_batch_swap(BatchCase* __restrict__ cases, BatchList l) {
 __global__ void __launch_bounds__(256) k_batch_finalize(BatchCase* __restrict__ cases) {
     __shared__ double red[256][6];
     const BatchCase& B = cases[blockIdx.x];
-    const int nsub = B.kind == 2 ? B.subcycles : 1;
+    const int nsub = B.kind != 0 ? B.subcycles : 1;
     finalize_block(1, B.nblk, B.partials, nsub, B.force, 0, red);
 }
 
@@ -1522,7 +1538,7 @@ __global__ void k_batch_rigid(BatchCase* __restrict__ cases, int n, int* __restr
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     const BatchCase& B = cases[c];
-    const double dt = B.kind == 2 ? (double)B.subcycles : 1.0;
+    const double dt = B.kind != 0 ? (double)B.subcycles : 1.0;
     rigid_one(B.g, B.part, B.prev, B.force, B.kd.rho0, B.gravity[0], B.gravity[1], B.gravity[2],
               dt, B.wall_contact, status);
 }
@@ -1574,11 +1590,11 @@ cudaError_t bulk_cpt(const void* src, void* dst, const Launch& L) {
     dim3 grid(L.g.ntx, L.g.nty, L.g.ntz);
     const auto& k = coll_of<typename std::conditional<(sizeof(T) < 4), C, T>::type, C>(L);
     if (L.nostream)
-        k_bulk<T, C, true, CPT><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
-                                                                L.parts, L.cp.np, L.all_tiles);
+        k_bulk<T, C, true, CPT><<<grid, L.block, 0, L.stream>>>(
+            (const T*)src, (T*)dst, L.g, k, L.parts, L.cp.np, L.all_tiles, L.status);
     else
-        k_bulk<T, C, false, CPT><<<grid, L.block, 0, L.stream>>>((const T*)src, (T*)dst, L.g, k,
-                                                                 L.parts, L.cp.np, L.all_tiles);
+        k_bulk<T, C, false, CPT><<<grid, L.block, 0, L.stream>>>(
+            (const T*)src, (T*)dst, L.g, k, L.parts, L.cp.np, L.all_tiles, L.status);
     return cudaGetLastError();
 }
 
@@ -1593,7 +1609,7 @@ cudaError_t bulk_t(const void* src, void* dst, const Launch& L) {
             dim3 grid((L.g.nx + 2 * PAIR_TX - 1) / (2 * PAIR_TX), (L.g.ny + PAIR_TY - 1) / PAIR_TY,
                       L.g.nz);
             k_bulk_pair<T><<<grid, dim3(PAIR_TX, PAIR_TY, 1), 0, L.stream>>>(
-                (const T*)src, (T*)dst, L.g, L.kf, L.parts, L.all_tiles ? 0 : L.cp.np);
+                (const T*)src, (T*)dst, L.g, L.kf, L.parts, L.all_tiles ? 0 : L.cp.np, L.status);
             return cudaGetLastError();
         }
     }
@@ -1798,13 +1814,13 @@ cudaError_t launch_batch_near(BatchCase* cases, BatchList l, long long total, in
     return cudaGetLastError();
 }
 cudaError_t launch_batch_bulk(int mode, BatchCase* cases, BatchList l, long long total, int grid,
-                              cudaStream_t s) {
+                              int* status, cudaStream_t s) {
     if (l.n == 0 || total == 0) return cudaSuccess;
     const unsigned gsz = (unsigned)(grid <= 0 || total < grid ? total : grid);
     if (mode == 3)
-        k_batch_bulk<3><<<gsz, 256, 0, s>>>(cases, l, total);
+        k_batch_bulk<3><<<gsz, 256, 0, s>>>(cases, l, total, status);
     else
-        k_batch_bulk<0><<<gsz, 256, 0, s>>>(cases, l, total);
+        k_batch_bulk<0><<<gsz, 256, 0, s>>>(cases, l, total, status);
     return cudaGetLastError();
 }
 cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s) {

@@ -159,6 +159,37 @@ inline Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) 
     return k;
 }
 
+// Checks of a configuration shared by every entry point that takes one
+// (lbm_create, lbm_sweep_noalloc): LBM_ERR_ARG for a value outside its
+// range, LBM_ERR_UNSUPPORTED for MEM MR within 0.01 of Lambda_- = 1/2.
+// Host-only; touches no device state.
+inline lbm_status check_config(const lbm_config& c) {
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1) return LBM_ERR_ARG;
+    if ((long long)c.nx * c.ny * c.nz > (1LL << 40)) return LBM_ERR_ARG;
+    if (!(c.tau > 0.5) || !std::isfinite(c.tau) || !(c.rho0 > 0.0) || !std::isfinite(c.rho0))
+        return LBM_ERR_ARG;
+    if (c.coupling < 0 || c.coupling > LBM_NONE) return LBM_ERR_ARG;
+    if (c.collision != LBM_BGK && c.collision != LBM_TRT) return LBM_ERR_ARG;
+    if (c.storage < LBM_STORE_F64 || c.storage > LBM_STORE_BF16S) return LBM_ERR_ARG;
+    if (c.bc_z < 0 || c.bc_z > 2 || (c.bc_z == 2 && c.nz < 3)) return LBM_ERR_ARG;
+    if (c.bc_z == 2 && !(std::isfinite(c.inflow[0]) && std::isfinite(c.inflow[1]) &&
+                         std::isfinite(c.inflow[2]) && c.rho_out > 0.0 && std::isfinite(c.rho_out)))
+        return LBM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(c.force_density[a]) || !std::isfinite(c.gravity[a])) return LBM_ERR_ARG;
+    if (c.subsample < 0 || c.subsample > 40 || c.lbm_subcycles < 0) return LBM_ERR_ARG;
+    if (c.collision == LBM_TRT) {
+        // Eq. (11): lambda_- from Lambda = magic; it must lie in (-2, 0)
+        const double lp = -1.0 / c.tau;
+        const double denom = c.magic / (0.5 + 1.0 / lp) - 0.5;
+        if (!(c.magic > 0.0) || !std::isfinite(c.magic) || denom == 0.0) return LBM_ERR_ARG;
+        const double lm = 1.0 / denom;
+        if (!(lm > -2.0 && lm < 0.0)) return LBM_ERR_ARG;
+    }
+    if (c.coupling == LBM_MEM_MR && !mr_supported(c)) return LBM_ERR_UNSUPPORTED;
+    return LBM_OK;
+}
+
 // Open-boundary data of a configuration (bc_z = 2) into the geometry.
 inline void set_open_boundaries(Geom& g, const lbm_config& cfg) {
     for (int a = 0; a < 3; ++a) {
@@ -176,7 +207,12 @@ enum : int {
     ST_REFILL_SOLID = 4,      // refill found no particle owning a cell (internal)
     ST_UNSTABLE = 8,          // a particle state became non-finite or too fast
     ST_BOUNDS = 16,           // an index check in a coupling kernel failed (access skipped)
+    ST_FLUID = 32,            // a fluid cell's density became non-finite or <= 0
 };
+static_assert(ST_TOO_MANY_OBJECTS == LBM_STATUS_TOO_MANY_OBJECTS && ST_DOMAIN == LBM_STATUS_DOMAIN &&
+                  ST_UNSTABLE == LBM_STATUS_UNSTABLE && ST_BOUNDS == LBM_STATUS_BOUNDS &&
+                  ST_FLUID == LBM_STATUS_FLUID,
+              "status bits of the public header");
 
 // storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision), 4 = FP16
 // and 5 = BF16 shifted populations f - w_q (FP32 arithmetic); launch_bulk
@@ -202,7 +238,7 @@ cudaError_t launch_batch_near(BatchCase* cases, BatchList l, long long total, in
                               int* status, cudaStream_t s);
 // mode 0 FP64 / 3 fixed-point collision; grid <= 0: one block per tile
 cudaError_t launch_batch_bulk(int mode, BatchCase* cases, BatchList l, long long total, int grid,
-                              cudaStream_t s);
+                              int* status, cudaStream_t s);
 cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s);
 cudaError_t launch_batch_finalize(BatchCase* cases, int n, cudaStream_t s);
 cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_t s);

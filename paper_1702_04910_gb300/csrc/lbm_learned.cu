@@ -280,7 +280,10 @@ __global__ void k_adam(float* __restrict__ P, float* __restrict__ M, float* __re
 }
 
 // Input mean and 1/std (FP64 sums in sample order; std < 1e-6 -> 1) and the
-// output scale (RMS of the targets, floored at 1e-12).
+// output scale: one RMS over the three force components and one over the
+// three torque components (samples in order, components in order within a
+// sample; floored at 1e-12), so that near-zero lateral targets keep their
+// physical size in the loss instead of being scaled up to unit size.
 __global__ void k_fit_norm(const float* __restrict__ X, const float* __restrict__ Tt, int n,
                            float* __restrict__ norm) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,13 +300,14 @@ __global__ void k_fit_norm(const float* __restrict__ X, const float* __restrict_
         norm[NORM_MU + t] = (float)mu;
         norm[NORM_IS + t] = (float)(sd > 1e-6 ? 1.0 / sd : 1.0);
     } else if (t < FIN + FOUT) {
-        const int k = t - FIN;
+        const int k = t - FIN, k0 = k < 3 ? 0 : 3;  // force or torque group
         double s2 = 0.0;
-        for (int s = 0; s < n; ++s) {
-            const double v = Tt[(long long)s * FOUT + k];
-            s2 += v * v;
-        }
-        const double r = sqrt(s2 / n);
+        for (int s = 0; s < n; ++s)
+            for (int j = k0; j < k0 + 3; ++j) {
+                const double v = Tt[(long long)s * FOUT + j];
+                s2 += v * v;
+            }
+        const double r = sqrt(s2 / (3.0 * n));
         norm[NORM_OS + k] = (float)(r > 1e-12 ? r : 1e-12);
     }
 }

@@ -36,6 +36,18 @@ static __device__ __align__(256) int g_status[64];
 constexpr size_t NOALLOC_MAP_ENTRIES = 1 << 20;  // geometry map, 2 MiB
 static __device__ __align__(256) unsigned short g_map[NOALLOC_MAP_ENTRIES];
 
+// Particle records passed by value to the kernel that stores them in
+// g_particles (32 x 160 B: within the 32 KiB kernel-argument limit).
+struct ParticleUpload {
+    DevParticle rec[MAX_PARTICLES];
+};
+static_assert(sizeof(ParticleUpload) <= 32000, "kernel argument too large");
+
+__global__ void k_upload_particles(ParticleUpload up, int n) {
+    const int i = threadIdx.x;
+    if (i < n && i < MAX_PARTICLES) g_particles[i] = up.rec[i];
+}
+
 constexpr int MAX_DEVICES = 64;
 struct Addresses {
     bool ready;
@@ -79,20 +91,18 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
         set_err(err, err_len, "null or aliased PDF buffers");
         return LBM_ERR_ARG;
     }
-    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || !(cfg->tau > 0.5) || !(cfg->rho0 > 0.0) ||
-        cfg->bc_z < 0 || cfg->bc_z > 2 || (cfg->bc_z == 2 && (cfg->nz < 3 || !(cfg->rho_out > 0.0))) ||
-        cfg->coupling < 0 || cfg->coupling > LBM_NONE ||
-        (cfg->collision != LBM_BGK && cfg->collision != LBM_TRT) || cfg->subsample < 0 ||
-        cfg->subsample > 64) {
-        set_err(err, err_len, "invalid configuration");
-        return LBM_ERR_ARG;
+    {
+        // the same checks as lbm_create
+        const lbm_status st = check_config(*cfg);
+        if (st != LBM_OK) {
+            set_err(err, err_len,
+                    st == LBM_ERR_UNSUPPORTED ? "MEM MR needs |Lambda_- - 1/2| >= 0.01"
+                                              : "invalid configuration");
+            return st;
+        }
     }
     if (cfg->storage != LBM_STORE_F64) {
         set_err(err, err_len, "lbm_sweep_noalloc takes FP64 PDF buffers only");
-        return LBM_ERR_UNSUPPORTED;
-    }
-    if (cfg->coupling == LBM_MEM_MR && !mr_supported(*cfg)) {
-        set_err(err, err_len, "MEM MR needs |Lambda_- - 1/2| >= 0.01");
         return LBM_ERR_UNSUPPORTED;
     }
     const bool coupled = cfg->coupling != LBM_NONE;
@@ -117,12 +127,16 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
     g.tz = 1;
     g.ntz = cfg->nz;
     double maxd = 0.0;
-    DevParticle recs[MAX_PARTICLES];
+    ParticleUpload up{};
     for (int i = 0; i < n; ++i) {
         const lbm_particle& p = particles_host[i];
         const double need = p.diameter + 2.0 * NEAR_HALO + 2.0;
         const double margin = g.bc_z == 2 ? OPEN_MARGIN : 0.0;
-        if (!(p.diameter >= 1.0) || !(p.density > 0.0) || need > g.nx || need > g.ny ||
+        bool finite = std::isfinite(p.diameter) && std::isfinite(p.density);
+        for (int a = 0; a < 3; ++a)
+            finite = finite && std::isfinite(p.x[a]) && std::isfinite(p.u[a]) &&
+                     std::isfinite(p.omega[a]);
+        if (!finite || !(p.diameter >= 1.0) || !(p.density > 0.0) || need > g.nx || need > g.ny ||
             (!g.bc_z && need > g.nz) ||
             (g.bc_z && (p.x[2] - 0.5 * p.diameter - margin < 0.0 ||
                         p.x[2] + 0.5 * p.diameter + margin > g.nz))) {
@@ -145,7 +159,7 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
         d.r = 0.5 * p.diameter;
         d.rho = p.density;
         d.fixed = p.fixed ? 1.0 : 0.0;
-        recs[i] = d;
+        up.rec[i] = d;
         maxd = std::max(maxd, p.diameter);
     }
     near_grid(g, maxd, L.box);
@@ -209,8 +223,10 @@ extern "C" lbm_status lbm_sweep_noalloc(const lbm_config* cfg, const double* src
         return LBM_ERR_CUDA;
     }
     if (n > 0) {
-        e = cudaMemcpyAsync(a.particles, recs, sizeof(DevParticle) * n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // recs lives on this stack frame
+        // the records travel as a kernel argument, copied at launch: nothing
+        // waits for the host array
+        k_upload_particles<<<1, MAX_PARTICLES, 0, s>>>(up, n);
+        e = cudaGetLastError();
         if (e == cudaSuccess) e = launch_regions(L);
         if (e == cudaSuccess) e = launch_map(L);
     }

@@ -38,10 +38,10 @@ def frame_shape(D: float):
     return (n_lat, n_lat, int(round(16.0 * D)))
 
 
-def _sim(D, coupling, collision, nu, u_inf, g, storage, stream):
+def _sim(D, coupling, collision, nu, u_inf, g, storage, stream, sub):
     kw = dict(coupling=coupling, collision=collision, tau=tau_from_nu(nu), magic=3.0 / 16.0,
               gravity=(0.0, 0.0, -g), rho0=1.0, bc_z=2, subsample=4,
-              subcycles=2 if coupling.startswith("MEM") else 1, wall_contact=0,
+              subcycles=sub, wall_contact=0,
               storage=storage, inflow=(0.0, 0.0, u_inf), rho_out=1.0)
     return Simulation(frame_shape(D), stream=stream, **kw)
 
@@ -60,11 +60,14 @@ def run_frame(D: float = 24.0, ga_target: float = 144.0, u_pv_ref: float = -1.28
               coupling: str = "MEM_CLI", collision: str | None = None, nu0: float = 0.01,
               density_ratio: float = 1.5, drag_tol: float = 1e-4, ga_tol: float = 1e-4,
               max_iter: int = 12, max_chunks: int = 80, free_t_refs: float = 20.0,
-              storage: str = "f64", stream=None, log=None):
+              storage: str = "f64", subcycles: int = 2, stream=None, log=None):
     """Calibration and release; returns a JSON-ready dict with u_pV.  PSM runs
-    use the BGK fluid part of Eq. (20) unless `collision` says otherwise."""
+    use the BGK fluid part of Eq. (20) unless `collision` says otherwise.
+    Every coupling runs `subcycles` LBM sweeps per step with their forces
+    averaged (Sec. 4.1: two); PSM with one sweep follows Algorithm 2 alone,
+    and then a free M3B2 sphere is unstable."""
     collision = collision or ("TRT" if coupling.startswith("MEM") else "BGK")
-    sub = 2 if coupling.startswith("MEM") else 1
+    sub = int(subcycles)
     re_ref = abs(u_pv_ref) * ga_target
     u_inf = re_ref * nu0 / D
     x0 = (2.67 * D, 2.67 * D, 5.34 * D)
@@ -77,7 +80,7 @@ def run_frame(D: float = 24.0, ga_target: float = 144.0, u_pv_ref: float = -1.28
     steps_total = 0
     g = 0.0
     for it in range(max_iter):
-        new = _sim(D, coupling, collision, nu, u_inf, 0.0, storage, stream)
+        new = _sim(D, coupling, collision, nu, u_inf, 0.0, storage, stream, sub)
         if s is None:
             new.init_equilibrium(1.0, (0.0, 0.0, u_inf))
             new.set_particles([part])
@@ -108,7 +111,7 @@ def run_frame(D: float = 24.0, ga_target: float = 144.0, u_pv_ref: float = -1.28
             break
         nu = nu * ga / ga_target
     # part two: release in the converged flow
-    free = _sim(D, coupling, collision, nu, u_inf, g, storage, stream)
+    free = _sim(D, coupling, collision, nu, u_inf, g, storage, stream, sub)
     p = dict(part)
     p["fixed"] = 0
     free.set_particles([p])
@@ -124,7 +127,8 @@ def run_frame(D: float = 24.0, ga_target: float = 144.0, u_pv_ref: float = -1.28
     tail = uz[int(0.8 * n_free):]
     u_pv = float((tail.mean() - u_inf) / u_ref)
     return {
-        "coupling": coupling, "collision": collision, "D": D, "shape": list(frame_shape(D)),
+        "coupling": coupling, "collision": collision, "subcycles": sub, "D": D,
+        "shape": list(frame_shape(D)),
         "Ga_target": ga_target, "Re_ref": re_ref, "u_inf": u_inf, "nu": nu,
         "tau": tau_from_nu(nu), "g": g, "u_ref": u_ref, "calibration": hist,
         "calibration_steps": steps_total, "free_steps": n_free, "u_pV": u_pv,

@@ -95,6 +95,8 @@ def test_enum_values_match_header():
         assert re.search(rf"LBM_{name}\s*=\s*{val}\b", text), name
     for st, name in binding.STATUS_NAMES.items():
         assert re.search(rf"{name}\s*=\s*{st}\b", text), name
+    for name, bit in binding.STATUS_BITS.items():
+        assert re.search(rf"{name}\s*=\s*{bit}\b", text), name
 
 
 def test_binding_wrapper_surface():
@@ -151,3 +153,75 @@ def test_batch_rejects_invalid_cases_without_gpu():
     assert st == binding.LBM_ERR_ARG and "case 1" in msg
     st, msg = create([], [])
     assert st == binding.LBM_ERR_ARG
+
+
+# ---- lbm_sweep_noalloc: host-side checks, with no GPU present ------------------------
+# These calls carry made-up device addresses.  Without a CUDA device nothing can
+# be dereferenced: a call that passes the checks stops at the device lookup
+# (LBM_ERR_CUDA).  With a device the same calls could launch kernels on those
+# addresses, so the tests only run where there is none.
+def _has_cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+no_device = pytest.mark.skipif(_has_cuda(), reason="runs only where no CUDA device exists")
+
+
+def _noalloc(cfg, parts):
+    err = ct.create_string_buffer(256)
+    lib = binding.load()
+    st = lib.lbm_sweep_noalloc(ct.byref(cfg), ct.c_void_p(0x1000), ct.c_void_p(0x2000),
+                               len(parts), binding.particles_to_c(parts),
+                               ct.c_void_p(0x3000), None, None, err, len(err))
+    return st, err.value.decode()
+
+
+def _spheres(n, D, L):
+    """n spheres of diameter D on a grid of an L^3 periodic box (overlaps allowed:
+    only the scratch check is exercised)."""
+    return [{"x": (4.0 + 7.0 * (i % 8), 4.0 + 7.0 * (i // 8), L / 2.0), "diameter": D,
+             "fixed": 1} for i in range(n)]
+
+
+@no_device
+def test_noalloc_scratch_limit_on_the_host():
+    """D = 24 in a 64^3 box: region extent E = ceil(D) + 6 = 30 cells per axis,
+    B = ceil(30/32) * ceil(30/2) * 30 = 450 near blocks, so n spheres need
+    n^2 * 450 * 6 doubles of force partials: 13 -> 456,300 fit the 524,288 of
+    the fixed scratch, 14 -> 529,200 do not.  One sphere of D = 100 in a 128^3
+    box needs 106^3 = 1,191,016 geometry-map entries, beyond the 1,048,576,
+    while its 4 * 53 * 106 * 6 = 134,832 partials fit."""
+    cfg = binding.make_config((64, 64, 64), coupling="PSM_M1B1", tau=0.8)
+    st, msg = _noalloc(cfg, _spheres(14, 24.0, 64))
+    assert st == binding.LBM_ERR_ARG and "force-partial" in msg and "529200" in msg, msg
+    st, msg = _noalloc(cfg, _spheres(13, 24.0, 64))
+    assert st == binding.LBM_ERR_CUDA, (st, msg)  # passed every check, then found no device
+    cfg = binding.make_config((128, 128, 128), coupling="MEM_CLI", tau=0.8)
+    st, msg = _noalloc(cfg, [{"x": (64.0, 64.0, 64.0), "diameter": 100.0, "fixed": 1}])
+    assert st == binding.LBM_ERR_ARG and "geometry-map" in msg, msg
+
+
+@no_device
+def test_noalloc_checks_the_configuration_as_lbm_create_does():
+    """The allocation-free sweep and lbm_create share their configuration checks:
+    a TRT collision needs Lambda > 0 (Eq. (11)), the supersampling at most 40^3,
+    finite body forces; MR is refused next to Lambda_- = 1/2."""
+    lib = binding.load()
+    h = ct.c_void_p()
+    bad = [dict(magic=0.0), dict(magic=-0.1), dict(subsample=41), dict(tau=0.5),
+           dict(fext=(float("nan"), 0.0, 0.0))]
+    for over in bad:
+        kw = dict(coupling="PSM_M2B2", tau=0.8)
+        kw.update(over)
+        cfg = binding.make_config((16, 16, 16), **kw)
+        assert lib.lbm_create(ct.byref(cfg), None, ct.byref(h)) == binding.LBM_ERR_ARG, over
+        st, msg = _noalloc(cfg, [])
+        assert st == binding.LBM_ERR_ARG and "configuration" in msg, (over, msg)
+    cfg = binding.make_config((16, 16, 16), coupling="MEM_MR", tau=0.875)
+    assert _noalloc(cfg, [])[0] == binding.LBM_ERR_UNSUPPORTED
+    cfg = binding.make_config((16, 16, 16), coupling="PSM_M2B2", tau=0.8, storage="f32")
+    assert _noalloc(cfg, [])[0] == binding.LBM_ERR_UNSUPPORTED

@@ -20,8 +20,8 @@ U_PV_FREE = -1.2345  # what the stand-in's released sphere does
 class StandIn:
     made = []
 
-    def __init__(self, D, coupling, collision, nu, u_inf, g, storage, stream):
-        self.D, self.nu, self.u_inf, self.g = D, nu, u_inf, g
+    def __init__(self, D, coupling, collision, nu, u_inf, g, storage, stream, sub):
+        self.D, self.nu, self.u_inf, self.g, self.sub = D, nu, u_inf, g, sub
         self.steps = 0
         self.closed = False
         self.particles = None
@@ -81,12 +81,15 @@ def test_calibration_reaches_the_target_galileo_number(stand_in):
     free = StandIn.made[-1]
     assert free.particles[0]["fixed"] == 0 and free.g == res["g"]
     u_ref = math.sqrt(0.5 * res["g"] * D)
-    sub = 2  # MEM: two LBM sweeps per global step
+    sub = 2  # two LBM sweeps per global step (Sec. 4.1)
+    assert res["subcycles"] == sub and all(s.sub == sub for s in StandIn.made)
     assert res["free_steps"] == int(20.0 * max(int(round(D / u_ref / sub)), 1))
 
 
-def test_psm_runs_bgk_and_one_sweep_per_step(stand_in):
-    res = frame.run_frame(D=10.0, coupling="PSM_M2B2", max_iter=30)
-    assert res["collision"] == "BGK"
+@pytest.mark.parametrize("sub", [1, 2])
+def test_psm_runs_bgk_with_the_requested_sweeps(stand_in, sub):
+    res = frame.run_frame(D=10.0, coupling="PSM_M2B2", max_iter=30, subcycles=sub)
+    assert res["collision"] == "BGK" and res["subcycles"] == sub
+    assert all(s.sub == sub for s in StandIn.made)
     u_ref = math.sqrt(0.5 * res["g"] * 10.0)
-    assert res["free_steps"] == int(20.0 * max(int(round(10.0 / u_ref)), 1))
+    assert res["free_steps"] == int(20.0 * max(int(round(10.0 / u_ref / sub)), 1))

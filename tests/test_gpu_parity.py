@@ -113,10 +113,12 @@ def moving_sphere_case(coupling, D=9.0, shape=(40, 36, 48), collision="TRT", fre
     return case
 
 
-# PSM M3B2 is exercised with prescribed motion: as printed (Eq. (25) with the
-# force of Eq. (28) and an explicit rigid-body update) its fully covered cells
-# reflect the relative momentum, j' - rho0 v = -(j - rho0 v), and the coupled
-# interior mode grows by 1 + 2 rho_f / rho_p per step for a free sphere.
+# PSM M3B2 with one sweep per step is exercised with prescribed motion: its
+# fully covered cells reflect the relative momentum, j' - rho0 v = -(j - rho0 v),
+# and with the force of Eq. (28) and an explicit rigid-body update the coupled
+# interior mode grows by 1 + 2 rho_f / rho_p per step for a free sphere.  With
+# the two averaged LBM subcycles of Sec. 4.1 the reflections of the two sweeps
+# cancel in the force and the free sphere is stable (test_psm_subcycles_parity).
 MOVING = [("PSM_M1B1", True), ("PSM_M2B2", True), ("PSM_M3B2", False), ("MEM_BB", True),
           ("MEM_CLI", True), ("MEM_CLI", False), ("MEM_MR", True), ("MEM_MR", False)]
 
@@ -256,6 +258,67 @@ def test_settling_full_size_parity(lattice, coupling, storage):
     compare_pdf(o, g)
     compare_forces(o, g, floor=1e-12)
     compare_particles(o, g)
+
+
+@pytest.mark.parametrize("coupling,storage", [("PSM_M1B1", "f64"), ("PSM_M2B2", "f64"),
+                                              ("MEM_BB", "f64"), ("MEM_CLI", "f64"),
+                                              ("MEM_MR", "f64"), ("MEM_CLI", "f64fx"),
+                                              ("PSM_M2B2", "f64fx")])
+def test_settling_full_size_window_with_remapping(lattice, coupling, storage):
+    """The full 128x128x512, D = 24 settling workload over a window in which
+    the sphere crosses more than a cell: released with a velocity of about
+    0.08 cells per unit time and a spin, under gravity, for 12 (MEM: 24
+    sweeps) or 32 (PSM) global steps.  MEM cells change owner and are
+    refilled, PSM solid fractions change; the mapping must agree bit for bit
+    and PDFs, forces and particle states within the FP64 bars."""
+    case = W.settling_sphere(coupling=coupling)
+    p = case["particles"][0]
+    p["u"] = (0.04, -0.03, -0.06)
+    p["omega"] = (0.002, -0.001, 0.003)
+    o, g = make_pair(case, storage=storage)
+    start(o, g, lattice)
+    mem = coupling.startswith("MEM")
+    before = o.solid() if mem else o.eps(0)
+    x0 = np.array(o.get_particles()[0]["x"])
+    for _ in range(12 if mem else 32):
+        o.step(1)
+        g.step(1)
+    moved = np.linalg.norm(np.array(o.get_particles()[0]["x"]) - x0)
+    assert moved > 1.0, moved
+    if mem:
+        after = o.solid()
+        assert np.count_nonzero(after != before) > 100
+        assert np.array_equal(g.flags(), after)
+    else:
+        after = o.eps(0)
+        assert np.count_nonzero(after != before) > 100
+        assert np.array_equal(g.eps(), after)
+    compare_pdf(o, g)
+    compare_forces(o, g)
+    compare_particles(o, g)
+    o.close()
+    g.close()
+
+
+@pytest.mark.parametrize("coupling,storage", [("PSM_M3B2", "f64"), ("PSM_M2B2", "f64"),
+                                              ("PSM_M1B1", "f64"), ("PSM_M3B2", "f64fx")])
+def test_psm_subcycles_parity(lattice, coupling, storage):
+    """PSM with the two LBM subcycles of the settling benchmark (Sec. 4.1):
+    both sweeps with the particle state of the start of the step, forces
+    averaged, the free sphere advanced by dt = 2; M3B2 included (stable with
+    the averaged force)."""
+    case = moving_sphere_case(coupling, free=True)
+    case["subcycles"] = 2
+    o, g = make_pair(case, storage=storage)
+    start(o, g, lattice, amp=0.02, seed=7)
+    for _ in range(15):
+        o.step(1)
+        g.step(1)
+    compare_pdf(o, g)
+    compare_forces(o, g)
+    compare_particles(o, g)
+    assert np.array_equal(g.eps(), o.eps(0))
+    assert np.all(np.isfinite(g.get_particles()[0]["u"]))
 
 
 # ---- checkpoint / restart gives bit-identical continuation --------------------------------

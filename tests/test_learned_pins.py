@@ -68,12 +68,18 @@ def test_fit_normalization_moments():
     X[:, 0] = np.arange(n)            # mean 4.5, std sqrt(8.25)
     X[:, 1] = 3.0                     # constant: std 0 -> 1/sigma = 1
     T = np.zeros((n, L.N_OUT))
-    T[:, 2] = np.where(np.arange(n) % 2, 2.0, -2.0)  # RMS 2
+    T[:, 2] = np.where(np.arange(n) % 2, 2.0, -2.0)  # force group: RMS sqrt(4/3)
     nrm = L.fit_normalization(X, T)
     mu, inv, s = L.split_norm(nrm)
     assert mu[0] == 4.5 and mu[1] == 3.0
     assert inv[0] == pytest.approx(1 / np.sqrt(8.25), rel=1e-15) and inv[1] == 1.0
-    assert s[2] == 2.0 and s[0] == 1e-12
+    # one scale per group: the force components share theirs, the (all zero)
+    # torque components take the floor
+    assert np.allclose(s[:3], np.sqrt(4.0 / 3.0), rtol=1e-15) and np.all(s[3:] == 1e-12)
+    T[:, 3] = 3.0
+    T[:, 5] = -4.0
+    s = L.split_norm(L.fit_normalization(X, T))[2]
+    assert np.allclose(s[3:], np.sqrt(25.0 / 3.0), rtol=1e-15)
 
 
 def _field(shape, vel_of, ind_of, rho0=1.0):

@@ -243,14 +243,18 @@ def test_uniform_translation_is_force_free(lattice, coupling):
 
 
 @pytest.mark.parametrize("coupling", ["PSM_M1B1", "PSM_M2B2", "PSM_M3B2"])
-def test_psm_momentum_balance(lattice, coupling):
-    """Momentum of a periodic box changes in one step by sum (1-B) f_ext minus
-    the PSM force Eq. (28): the solid term is the only exchange with the sphere."""
+@pytest.mark.parametrize("subcycles", [1, 2])
+def test_psm_momentum_balance(lattice, coupling, subcycles):
+    """Momentum of a periodic box changes per sweep by sum (1-B) f_ext minus
+    the PSM force Eq. (28): the solid term is the only exchange with the
+    sphere.  With two subcycles (Sec. 4.1) the step reports the mean force of
+    its two sweeps."""
     c, w, _ = lattice
     shape = (14, 13, 12)
     tau = 0.9
     fext = np.array([2e-5, 1e-5, -1e-5])
-    o = Oracle(shape, coupling=coupling, collision="BGK", tau=tau, fext=fext)
+    o = Oracle(shape, coupling=coupling, collision="BGK", tau=tau, fext=fext,
+               subcycles=subcycles)
     o.set_particles([{"x": (6.9, 6.3, 5.8), "u": (0.01, 0, -0.02), "omega": (0, 0.003, 0.001),
                       "diameter": 6.2, "fixed": 1}])
     f0 = W.perturbed_field(w, shape, 0.03, seed=5)
@@ -262,7 +266,7 @@ def test_psm_momentum_balance(lattice, coupling):
     F, _ = o.forces()
     _, j1 = moments(o.pdf("pre"), c)
     dJ = j1.reshape(3, -1).sum(axis=1) - j0.reshape(3, -1).sum(axis=1)
-    expect = fext * (1.0 - B).sum() - F[0]
+    expect = subcycles * (fext * (1.0 - B).sum() - F[0])
     assert np.allclose(dJ, expect, atol=1e-13)
     assert np.max(np.abs(F)) > 1e-4  # the exchange is not trivially zero
 
@@ -441,6 +445,40 @@ def test_angular_momentum_balance(lattice, coupling):
     sweeps = 2 if mem else 1
     assert np.allclose(L1 - L0, -sweeps * T[0], rtol=0, atol=1e-13)
     assert np.max(np.abs(T[0])) > 1e-3  # the exchange is not trivially zero
+
+
+@pytest.mark.parametrize("subcycles", [1, 2])
+def test_free_m3b2_sphere_needs_averaged_subcycles(subcycles):
+    """M3 of Eq. (25) reflects the relative momentum of a fully covered cell,
+    j' - rho0 v = -(j - rho0 v), and Eq. (28) hands that exchange to the
+    particle.  With one sweep per step and the explicit update of Sec. 4.1 the
+    coupled interior mode grows by 1 + 2 rho_f/rho_p per step: a free sphere
+    diverges within a few tens of steps.  With the two LBM subcycles whose
+    forces Sec. 4.1 averages, the reflections of the two sweeps cancel and
+    the sphere settles like the M2B2 one (within 10 % after 150 steps)."""
+    def run(coupling, sub):
+        case = W.settling_sphere(D=8.0, shape=(24, 24, 48), ga=40.0, nu=0.02,
+                                 drop_below_top=12.0, coupling=coupling)
+        kw = W.sim_kwargs(case)
+        kw["subcycles"] = sub
+        o = Oracle(case["shape"], **kw)
+        o.set_particles(case["particles"])
+        o.init_equilibrium()
+        u = []
+        for _ in range(150 // sub):
+            st = o.step(1)
+            u.append(o.get_particles()[0]["u"][2])
+            if st != 0 or not np.isfinite(u[-1]) or abs(u[-1]) > 1.0:
+                break
+        o.close()
+        return np.array(u)
+    u3 = run("PSM_M3B2", subcycles)
+    if subcycles == 1:
+        assert not (np.all(np.isfinite(u3)) and np.max(np.abs(u3)) < 1.0 and len(u3) == 150)
+    else:
+        u2 = run("PSM_M2B2", 2)
+        assert len(u3) == len(u2) and np.all(np.isfinite(u3))
+        assert abs(u3[-1] - u2[-1]) < 0.1 * abs(u2[-1]), (u3[-1], u2[-1])
 
 
 def test_refilled_cells_carry_body_velocity(lattice):

@@ -3,11 +3,12 @@
 lbm_sweep_noalloc serves callers that cannot allocate device memory while
 they step -- a program that owns all device memory through its own pool, or a
 loop that cannot take the device-wide synchronisation of cudaFree.  It keeps
-its scratch (the per-tile force partials) in a fixed device array instead.
-Here it must reproduce, on two calls in a row, the sweep and the force total
-that lbm_step computes through a handle, within the parity tolerances used
-elsewhere (PDFs 1e-12 relative, forces 1e-10 relative).  This file is named
-to be collected last.
+its scratch (the per-block force partials, the geometry map, the particle
+records) in fixed device arrays instead.  Here it must reproduce, on two calls
+in a row, the sweep and the force total that lbm_step computes through a
+handle, within the parity tolerances used elsewhere (PDFs 1e-12 relative,
+forces 1e-10 relative), leave the device's free memory unchanged, and raise
+no status bit.  This file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -51,49 +52,57 @@ def test_noalloc_sweep_matches_handle_step(lattice, coupling):
     ref1, (F1, T1) = sim.pdf(), sim.forces()
     sim.step(1)
     ref2, (F2, T2) = sim.pdf(), sim.forces()
+    # solid cells are not updated by a MEM sweep: compare fluid cells
+    fluid = (sim.flags() == 0) if coupling.startswith("MEM") else np.ones(case["shape"][::-1], bool)
     sim.close()
 
     cfg = B.make_config(case["shape"], **kw)
     bufs = [torch.from_numpy(state0).cuda(), torch.empty_like(torch.from_numpy(state0)).cuda()]
     ft = torch.zeros(6, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
+    free = []
     for call, (ref, F, T) in enumerate(((ref1, F1, T1), (ref2, F2, T2))):
         src, dst = bufs[call % 2], bufs[(call + 1) % 2]
+        free.append(torch.cuda.mem_get_info()[0])
         B.lbm_sweep_noalloc(cfg, src.data_ptr(), dst.data_ptr(), case["particles"], ft.data_ptr(),
-                            stream=stream)
+                            status_ptr=status.data_ptr(), stream=stream)
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         got = dst.cpu().numpy()
-        if coupling.startswith("MEM"):
-            # solid cells are not updated by a sweep: compare fluid cells
-            sim2 = B.Simulation(case["shape"], stream=stream, **kw)
-            sim2.set_particles(case["particles"])
-            flags = sim2.flags() == 0
-            sim2.close()
-        else:
-            flags = np.ones(case["shape"][::-1], dtype=bool)
-        err = np.max(np.abs(got[:, flags] - ref[:, flags])) / np.max(np.abs(ref[:, flags]))
+        err = np.max(np.abs(got[:, fluid] - ref[:, fluid])) / np.max(np.abs(ref[:, fluid]))
         assert err <= PDF_TOL, (call, err)
         out = ft.cpu().numpy()
         ferr = np.linalg.norm(out[:3] - F[0]) / np.linalg.norm(F[0])
         R = 0.5 * case["particles"][0]["diameter"]
         terr = np.linalg.norm(out[3:] - T[0]) / max(np.linalg.norm(T[0]), np.linalg.norm(F[0]) * R)
         assert ferr <= FORCE_TOL and terr <= FORCE_TOL, (call, ferr, terr)
+        assert int(status.item()) == 0
+    # the first call may load the library's device code (and with it the fixed
+    # scratch); from then on the device's free memory does not move
+    assert free[1] == free[2] == free[3], free
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch():
-    """32 spheres of D = 24 need 32^2 x 120 x 6 doubles of force partials,
-    more than the fixed 524,288: rejected before any device work, so the
-    (deliberately tiny) buffers below are never touched."""
+    """14 spheres of D = 24 in a 64^3 box need 14^2 x 450 x 6 = 529,200
+    doubles of force partials (region extent 30 cells, 450 near blocks per
+    region), more than the fixed 524,288: rejected before any device work.  The
+    buffers have the sizes the call declares, so even a call that got past the
+    check would stay inside them."""
     import torch
 
     from paper_1702_04910_gb300 import binding as B
 
-    cfg = B.make_config((256, 256, 256), coupling="PSM_M1B1", tau=0.8)
-    dummy = torch.zeros(2, dtype=torch.float64, device="cuda")
-    ft = torch.zeros(6 * 32, dtype=torch.float64, device="cuda")
-    parts = [{"x": (16.0 + 32.0 * (i % 8), 64.0 + 128.0 * (i // 16), 64.0 + 128.0 * ((i // 8) % 2)),
-              "diameter": 24.0, "fixed": 1} for i in range(32)]
+    shape = (64, 64, 64)
+    cfg = B.make_config(shape, coupling="PSM_M1B1", tau=0.8)
+    n = 14
+    src = torch.zeros(19 * 64 ** 3, dtype=torch.float64, device="cuda")
+    dst = torch.zeros_like(src)
+    ft = torch.zeros(6 * n, dtype=torch.float64, device="cuda")
+    parts = [{"x": (4.0 + 7.0 * (i % 8), 4.0 + 7.0 * (i // 8), 32.0), "diameter": 24.0,
+              "fixed": 1} for i in range(n)]
     with pytest.raises(B.LbmError) as ei:
-        B.lbm_sweep_noalloc(cfg, dummy.data_ptr(), dummy[1:].data_ptr(), parts, ft.data_ptr())
+        B.lbm_sweep_noalloc(cfg, src.data_ptr(), dst.data_ptr(), parts, ft.data_ptr())
     assert ei.value.status == B.LBM_ERR_ARG
-    assert "scratch" in str(ei.value)
+    assert "scratch" in str(ei.value) and "529200" in str(ei.value)
+    assert not dst.any().item()  # nothing ran
