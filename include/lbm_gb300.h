@@ -421,7 +421,9 @@ const char *lbm_batch_last_error(const lbm_batch *b);
  * y^ = W3 h2 + b3; y = y^ * s_out.  FP32 parameters, [in][out] layout:
  * W1 (512x64), b1, W2 (64x64), b2, W3 (64x6), b3 (LBM_MLP_PARAMS floats).
  * Normalisation block (LBM_MLP_NORM floats): mu[512], 1/sigma[512], s_out[6].
- * Loss: L = 1/(2n) sum_s |y^_s - t_s / s_out|^2. */
+ * Loss: L = 1/(2n) sum_s sum_k w_k (y^_sk - t_sk / s_out_k)^2 with
+ * w_k = (s_out_k / max_j s_out_j)^2: each output has its own scale, and its
+ * error counts in the units of the largest target. */
 #define LBM_MLP_IN 512
 #define LBM_MLP_HIDDEN 64
 #define LBM_MLP_OUT 6
@@ -444,9 +446,7 @@ lbm_status lbm_mlp_set_normalization(lbm_mlp *m, const float *host, size_t count
 lbm_status lbm_mlp_get_normalization(lbm_mlp *m, float *host, size_t count);
 
 /* Fits the normalisation to n samples on the device: mu and 1/sigma per input
- * (sigma < 1e-6 -> 1); s_out = one RMS over the three force targets and one
- * over the three torque targets (floored at 1e-12), so each component keeps
- * its physical size in the loss.
+ * (sigma < 1e-6 -> 1), s_out = RMS of each target (floored at 1e-12).
  * x_dev: n x LBM_MLP_IN floats; t_dev: n x LBM_MLP_OUT floats. */
 lbm_status lbm_mlp_fit_normalization(lbm_mlp *m, const float *x_dev, const float *t_dev, int n);
 

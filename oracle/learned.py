@@ -9,7 +9,8 @@ code with it.
 The paper has no learned component.  This follows the extension's contract
 (stated in the library's header): a 512-feature near-surface stencil of a
 sphere -> MLP 512-64-64-6 with tanh -> correction of the hydrodynamic force
-and torque, trained by full-batch Adam on L = 1/(2n) sum |y^ - t/s|^2.
+and torque, trained by full-batch Adam on
+L = 1/(2n) sum_s sum_k w_k (y^_sk - t_sk/s_k)^2 with w_k = (s_k / max_j s_j)^2.
 Everything here is NumPy in float64, one operation per line of the
 definition, no blocking or fusion.
 """
@@ -62,12 +63,20 @@ def forward(P, norm, X):
     return {"xh": xh, "h1": h1, "h2": h2, "yh": yh, "y": yh * s_out}
 
 
+def loss_weights(s_out):
+    """w_k = (s_k / max_j s_j)^2: the loss of output k in the physical units
+    of the largest target (the targets are dimensionless already), while each
+    output keeps its own scale s_k."""
+    s_out = np.asarray(s_out, dtype=np.float64)
+    return (s_out / s_out.max()) ** 2
+
+
 def loss(P, norm, X, T):
-    """L = 1/(2n) sum_s sum_k (y^_sk - t_sk / s_k)^2."""
+    """L = 1/(2n) sum_s sum_k w_k (y^_sk - t_sk / s_k)^2."""
     _, _, s_out = split_norm(norm)
     a = forward(P, norm, X)
     e = a["yh"] - np.asarray(T, dtype=np.float64) / s_out
-    return 0.5 * np.sum(e * e) / e.shape[0]
+    return 0.5 * np.sum(loss_weights(s_out) * e * e) / e.shape[0]
 
 
 def gradient(P, norm, X, T):
@@ -76,7 +85,7 @@ def gradient(P, norm, X, T):
     _, _, s_out = split_norm(norm)
     a = forward(P, norm, X)
     n = a["yh"].shape[0]
-    d3 = (a["yh"] - np.asarray(T, dtype=np.float64) / s_out) / n  # dL/dy^
+    d3 = loss_weights(s_out) * (a["yh"] - np.asarray(T, dtype=np.float64) / s_out) / n  # dL/dy^
     gW3 = a["h2"].T @ d3
     gb3 = d3.sum(axis=0)
     d2 = (d3 @ W3.T) * (1.0 - a["h2"] ** 2)  # dL/dz2 (tanh' = 1 - tanh^2)
@@ -98,20 +107,17 @@ def adam(P, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def fit_normalization(X, T):
-    """mu and 1/sigma per input (sigma < 1e-6 -> 1).  Output scale: one RMS
-    for the three force components together and one for the three torque
-    components (>= 1e-12), so that the loss weighs each component by its
-    physical size -- a per-component RMS would blow near-zero lateral targets
-    up to the size of the drag correction."""
+    """mu and 1/sigma per input (sigma < 1e-6 -> 1); output scale s_k = RMS of
+    target k (>= 1e-12).  Each output is scaled to its own target, so a
+    near-zero lateral target is predicted near zero; the loss weights
+    (loss_weights) keep such components from dominating the fit."""
     X = np.asarray(X, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
     mu = X.mean(axis=0)
     sd = np.sqrt(((X - mu) ** 2).mean(axis=0))
     inv = np.where(sd > 1e-6, 1.0 / np.where(sd > 1e-6, sd, 1.0), 1.0)
-    rms_f = np.sqrt((T[:, :3] * T[:, :3]).mean())
-    rms_t = np.sqrt((T[:, 3:] * T[:, 3:]).mean())
-    s = np.array([rms_f] * 3 + [rms_t] * 3)
-    return np.concatenate([mu, inv, np.maximum(s, 1e-12)])
+    rms = np.sqrt((T * T).mean(axis=0))
+    return np.concatenate([mu, inv, np.maximum(rms, 1e-12)])
 
 
 # ---- feature stencil ----------------------------------------------------------------

@@ -87,12 +87,12 @@ struct Coll {
     C alpha, beta;    // 1 + (l+ + l-)/2, (l+ - l-)/2
     C hs, hd;         // (alpha + beta)/2 = (1 + l+)/2, (alpha - beta)/2 = (1 + l-)/2
     C c0;             // 1 + l+
-    C m15r0;          // -3/2 rho0
+    C m15r0;          // -3/2 / rho0 (multiplies j.j, j = rho0 U)
     C lpw[3];         // l+ w_k, k = rest, axis, diagonal
-    C k1w[3];         // 9/2 l+ w_k rho0
-    C k2w[3];         // 3 l- w_k rho0
-    C hw[3];          // 3 w_k (times U.f_ext)
-    C gq[10];         // 9 w_q (c_q . f_ext), q = 1,3,...,17 (index (q-1)/2)
+    C k1w[3];         // 9/2 l+ w_k / rho0 (multiplies (c.j)^2)
+    C k2w[3];         // 3 l- w_k (multiplies c.j)
+    C hw[3];          // 3 w_k / rho0 (times j.f_ext)
+    C gq[10];         // 9 w_q (c_q . f_ext) / rho0, q = 1,3,...,17 (index (q-1)/2)
     C fq[10];         // 3 w_q (c_q . f_ext)
 };
 
@@ -517,6 +517,22 @@ __device__ __forceinline__ void moments(const C (&f)[NQ], const Coll<C>& k, C& r
     uz = ((d5 + d11) - (d13 - d15) - d17) * k.inv_rho0;
 }
 
+// Density and momentum j = rho0 U of Eq. (4) (the collision works with j and
+// constants that carry the 1/rho0: three products fewer per cell).
+template <typename C>
+__device__ __forceinline__ void moments_j(const C (&f)[NQ], C& rho, C& jx, C& jy, C& jz) {
+    C s1 = f[1] + f[2], s3 = f[3] + f[4], s5 = f[5] + f[6], s7 = f[7] + f[8];
+    C s9 = f[9] + f[10], s11 = f[11] + f[12], s13 = f[13] + f[14], s15 = f[15] + f[16];
+    C s17 = f[17] + f[18];
+    rho = f[0] + ((s1 + s3) + (s5 + s7)) + ((s9 + s11) + (s13 + s15)) + s17;
+    C d1 = f[1] - f[2], d3 = f[3] - f[4], d5 = f[5] - f[6], d7 = f[7] - f[8];
+    C d9 = f[9] - f[10], d11 = f[11] - f[12], d13 = f[13] - f[14], d15 = f[15] - f[16];
+    C d17 = f[17] - f[18];
+    jx = (d1 + d7) + (d9 + d11) + d13;
+    jy = (d3 + d7) - (d9 - d15) + d17;
+    jz = (d5 + d11) - (d13 - d15) - d17;
+}
+
 // ---- fluid collision Eq. (1) with TRT Eq. (9)-(10) (BGK: lambda_- = lambda_+)
 // and forcing Eq. (7), in place, written per opposite pair (q, qbar):
 //   f^eq,+ = w (rho + rho0 (9/2 (c.U)^2 - 3/2 U.U)),  f^eq,- = 3 w rho0 c.U,
@@ -578,10 +594,12 @@ __device__ __forceinline__ bool density_bad(fx64 r) {
 
 // Returns true when the cell's density is not finite and positive.
 // SHIFTED: f holds the shifted populations f_q - w_q, whose sum is rho - 1.
+// Written in j = rho0 U (ux, uy, uz below hold j); the constants k1w, k2w,
+// m15r0, hw and gq carry the powers of 1/rho0 that U would bring.
 template <typename C, bool FORCE, bool SHIFTED>
 __device__ __forceinline__ bool collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
     C rho, ux, uy, uz;
-    moments(f, k, rho, ux, uy, uz);
+    moments_j(f, rho, ux, uy, uz);
     const bool bad = SHIFTED ? density_bad(rho + (C)1) : density_bad(rho);
     if constexpr (PairSumDiff<C>::value && !FORCE) {
         // products shared between pairs: with t_a = k1w_diag u_a^2 and

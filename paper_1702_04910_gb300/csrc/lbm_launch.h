@@ -143,17 +143,17 @@ inline Coll<C> make_coll(double lp, double lm, double rho0, const double fe[3]) 
     k.hs = (C)(0.5 * (1.0 + lp));
     k.hd = (C)(0.5 * (1.0 + lm));
     k.c0 = (C)(1.0 + lp);
-    k.m15r0 = (C)(-1.5 * rho0);
+    k.m15r0 = (C)(-1.5 / rho0);
     const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
     for (int c = 0; c < 3; ++c) {
         k.lpw[c] = (C)(lp * w[c]);
-        k.k1w[c] = (C)(4.5 * lp * w[c] * rho0);
-        k.k2w[c] = (C)(3.0 * lm * w[c] * rho0);
-        k.hw[c] = (C)(3.0 * w[c]);
+        k.k1w[c] = (C)(4.5 * lp * w[c] / rho0);
+        k.k2w[c] = (C)(3.0 * lm * w[c]);
+        k.hw[c] = (C)(3.0 * w[c] / rho0);
     }
     for (int q = 1; q < NQ; q += 2) {
         const double cf = cx(q) * fe[0] + cy(q) * fe[1] + cz(q) * fe[2];
-        k.gq[(q - 1) / 2] = (C)(9.0 * wq(q) * cf);
+        k.gq[(q - 1) / 2] = (C)(9.0 * wq(q) * cf / rho0);
         k.fq[(q - 1) / 2] = (C)(3.0 * wq(q) * cf);
     }
     return k;

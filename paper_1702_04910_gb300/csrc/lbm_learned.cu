@@ -184,9 +184,10 @@ __global__ void __launch_bounds__(FH)
     }
 }
 
-// Backward deltas of the loss L = 1/(2n) sum_s sum_k (y^_sk - t_sk / os_k)^2
-// (one 64-thread block per sample): D3 = dL/dz3, D2 = dL/dz2, D1 = dL/dz1
-// (z: pre-activations), and the sample's loss term.
+// Backward deltas of the loss L = 1/(2n) sum_s sum_k w_k (y^_sk - t_sk / os_k)^2,
+// w_k = (os_k / max_j os_j)^2 (each output's error in the units of the
+// largest target), one 64-thread block per sample: D3 = dL/dz3, D2 = dL/dz2,
+// D1 = dL/dz1 (z: pre-activations), and the sample's loss term.
 __global__ void __launch_bounds__(FH)
     k_mlp_delta(const float* __restrict__ P, const float* __restrict__ norm,
                 const float* __restrict__ Tt, int n, const float* __restrict__ H1,
@@ -198,15 +199,18 @@ __global__ void __launch_bounds__(FH)
     if (smp >= n) return;
     const float inv_n = 1.0f / (float)n;
     if (u < FOUT) {
+        float smax = norm[NORM_OS];
+        for (int k = 1; k < FOUT; ++k) smax = fmaxf(smax, norm[NORM_OS + k]);
+        const float r = norm[NORM_OS + u] / smax, w = r * r;
         const float e = Yn[(long long)smp * FOUT + u] - Tt[(long long)smp * FOUT + u] / norm[NORM_OS + u];
-        e3[u] = e;
-        d3[u] = e * inv_n;
-        D3[(long long)smp * FOUT + u] = e * inv_n;
+        e3[u] = w * e * e;
+        d3[u] = w * e * inv_n;
+        D3[(long long)smp * FOUT + u] = w * e * inv_n;
     }
     __syncthreads();
     if (u == 0) {
         double l = 0.0;
-        for (int k = 0; k < FOUT; ++k) l += 0.5 * (double)e3[k] * (double)e3[k];
+        for (int k = 0; k < FOUT; ++k) l += 0.5 * (double)e3[k];
         loss_s[smp] = l;
     }
     float a = 0.0f;
@@ -280,10 +284,7 @@ __global__ void k_adam(float* __restrict__ P, float* __restrict__ M, float* __re
 }
 
 // Input mean and 1/std (FP64 sums in sample order; std < 1e-6 -> 1) and the
-// output scale: one RMS over the three force components and one over the
-// three torque components (samples in order, components in order within a
-// sample; floored at 1e-12), so that near-zero lateral targets keep their
-// physical size in the loss instead of being scaled up to unit size.
+// output scale: the RMS of each target (samples in order; floored at 1e-12).
 __global__ void k_fit_norm(const float* __restrict__ X, const float* __restrict__ Tt, int n,
                            float* __restrict__ norm) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -300,14 +301,13 @@ __global__ void k_fit_norm(const float* __restrict__ X, const float* __restrict_
         norm[NORM_MU + t] = (float)mu;
         norm[NORM_IS + t] = (float)(sd > 1e-6 ? 1.0 / sd : 1.0);
     } else if (t < FIN + FOUT) {
-        const int k = t - FIN, k0 = k < 3 ? 0 : 3;  // force or torque group
+        const int k = t - FIN;
         double s2 = 0.0;
-        for (int s = 0; s < n; ++s)
-            for (int j = k0; j < k0 + 3; ++j) {
-                const double v = Tt[(long long)s * FOUT + j];
-                s2 += v * v;
-            }
-        const double r = sqrt(s2 / (3.0 * n));
+        for (int s = 0; s < n; ++s) {
+            const double v = Tt[(long long)s * FOUT + k];
+            s2 += v * v;
+        }
+        const double r = sqrt(s2 / n);
         norm[NORM_OS + k] = (float)(r > 1e-12 ? r : 1e-12);
     }
 }

@@ -49,7 +49,8 @@ def test_zero_weights_closed_form():
     g = L.gradient(P0, norm, X, T)
     gW1, gb1, gW2, gb2, gW3, gb3 = L.unpack(g)
     assert not gW1.any() and not gW2.any() and not gb1.any() and not gb2.any()
-    assert np.allclose(gb3, (b3 - T / s_out).mean(axis=0), atol=1e-15)
+    w = (s_out / s_out.max()) ** 2
+    assert np.allclose(gb3, w * (b3 - T / s_out).mean(axis=0), atol=1e-15)
     assert np.allclose(gW3, np.tanh(b2)[:, None] * gb3[None, :], atol=1e-15)
 
 
@@ -68,18 +69,16 @@ def test_fit_normalization_moments():
     X[:, 0] = np.arange(n)            # mean 4.5, std sqrt(8.25)
     X[:, 1] = 3.0                     # constant: std 0 -> 1/sigma = 1
     T = np.zeros((n, L.N_OUT))
-    T[:, 2] = np.where(np.arange(n) % 2, 2.0, -2.0)  # force group: RMS sqrt(4/3)
+    T[:, 2] = np.where(np.arange(n) % 2, 2.0, -2.0)  # RMS 2
+    T[:, 4] = 0.5
     nrm = L.fit_normalization(X, T)
     mu, inv, s = L.split_norm(nrm)
     assert mu[0] == 4.5 and mu[1] == 3.0
     assert inv[0] == pytest.approx(1 / np.sqrt(8.25), rel=1e-15) and inv[1] == 1.0
-    # one scale per group: the force components share theirs, the (all zero)
-    # torque components take the floor
-    assert np.allclose(s[:3], np.sqrt(4.0 / 3.0), rtol=1e-15) and np.all(s[3:] == 1e-12)
-    T[:, 3] = 3.0
-    T[:, 5] = -4.0
-    s = L.split_norm(L.fit_normalization(X, T))[2]
-    assert np.allclose(s[3:], np.sqrt(25.0 / 3.0), rtol=1e-15)
+    assert s[2] == 2.0 and s[4] == 0.5 and s[0] == 1e-12
+    # loss weights: each output's error in the units of the largest target
+    assert np.allclose(L.loss_weights(s), (s / 2.0) ** 2, rtol=0, atol=1e-30)
+    assert L.loss_weights(s)[2] == 1.0 and L.loss_weights(s)[4] == 0.0625
 
 
 def _field(shape, vel_of, ind_of, rho0=1.0):
