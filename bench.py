@@ -224,13 +224,18 @@ def run_learned(args, stream):
     from paper_1702_04910_gb300 import learned as LR
 
     full = args.learned == "full"
-    res = LR.experiment(train_ga=[110.0, 170.0, 240.0], test_ga=[140.0, 210.0],
+    # "full" trains on five Galileo numbers (one on each side of both
+    # held-out values); "small" on three
+    train = [110.0, 130.0, 170.0, 190.0, 240.0] if full else [110.0, 170.0, 240.0]
+    res = LR.experiment(train_ga=train, test_ga=[140.0, 210.0],
                         coupling="PSM_M2B2", D_c=12.0 if full else 6.0, ratio=4,
-                        t_refs=6.0 if full else 5.0, train_steps=3000, stream=stream,
+                        t_refs=6.0 if full else 5.0, train_steps=8000 if full else 3000,
+                        stream=stream,
                         coarse_storage="f32" if full else "f64")
     res.pop("model").close()
     held = {g: r for g, r in res["cases"].items() if r["held_out"]}
     return {
+        "train_ga": res["train_ga"],
         "workload": f"settling sphere Ga {res['test_ga']} held out; coarse D={res['D_coarse']:.0f} "
                     f"({res['coarse_storage']}) corrected towards D={res['D_fine']:.0f} (f64), "
                     f"{res['coupling']}",

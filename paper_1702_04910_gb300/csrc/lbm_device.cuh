@@ -586,8 +586,9 @@ __device__ __forceinline__ bool density_bad(double r) {
 __device__ __forceinline__ bool density_bad(float r) {
     return __float_as_uint(r) - 1u >= 0x7F7FFFFFu;
 }
-// fixed point cannot hold NaN; a saturated conversion or a wrapped sum shows
-// as a density outside (0, 16)
+// fixed point cannot hold NaN (the conversion from FP64 turns a non-finite
+// value into 0); a saturated conversion or a wrapped sum shows as a density
+// outside (0, 16)
 __device__ __forceinline__ bool density_bad(fx64 r) {
     return !(r.v > 0 && r.v < (16LL << FX_SHIFT));
 }

@@ -7,10 +7,15 @@
 //   + and -   exact two-instruction integer adds;
 //   *         32 x 32 -> 64-bit partial products, rounded to nearest at
 //             2^-58: unbiased, error within 1 unit of 2^-58 (3.5e-18);
-//   FP64 in   the 53-bit significand shifted by the exponent (integer ops);
-//   FP64 out  normalised with a leading-zero count, rounded to nearest.
+//   FP64 in   x 2^58 by adding 58 to the exponent field (one integer add on
+//             the high word), then the hardware conversion to a 64-bit
+//             integer, rounded to nearest even;
+//   FP64 out  the hardware conversion of the integer (rounded to nearest
+//             even), then 58 subtracted from the exponent field; zero stays
+//             zero.
 // Values of magnitude >= 32 saturate on input (the state is then unphysical
-// anyway: LBM populations are O(w_q)).
+// anyway: LBM populations are O(w_q)); a non-finite input becomes 0 (its
+// exponent field wraps when 58 is added, leaving a tiny value).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,35 +45,18 @@ struct fx64 {
 
     __device__ explicit operator double() const { return to_double(v); }
 
+    // Exponent moves are exact for every value the sweep meets: a nonzero
+    // fixed-point value is at least 2^-58 (a normal double), and zero maps
+    // to 2^(58 - 1023) on input, which converts to 0.
     __device__ static __forceinline__ long long from_double(double d) {
-        const long long b = __double_as_longlong(d);
-        const int e = (int)((b >> 52) & 0x7FF);
-        const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-        const int sh = e - (1075 - FX_SHIFT);  // x 2^58 = m 2^sh
-        long long r;
-        if (e == 0)
-            r = 0;
-        else if (sh >= 0)
-            r = sh < 10 ? (m << sh) : 0x7FFFFFFFFFFFFFFFLL;
-        else
-            r = sh > -63 ? (m >> (-sh)) : 0;
-        return b < 0 ? -r : r;
+        const int hi = __double2hiint(d) + (FX_SHIFT << 20);
+        return __double2ll_rn(__hiloint2double(hi, __double2loint(d)));
     }
 
     __device__ static __forceinline__ double to_double(long long v) {
-        if (v == 0) return 0.0;
-        const unsigned long long sgn = v < 0 ? (1ULL << 63) : 0ULL;
-        unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-        int p = 63 - __clzll((long long)u);  // top bit: value in [2^(p-58), 2^(p-57))
-        if (p > 52) {
-            u += 1ULL << (p - 53);  // round to nearest (ties away from zero)
-            if (u >> (p + 1)) ++p;  // carried into a new top bit
-            u >>= (p - 52);
-        } else {
-            u <<= (52 - p);
-        }
-        const unsigned long long e = (unsigned long long)(p - FX_SHIFT + 1023);
-        return __longlong_as_double((long long)(sgn | (e << 52) | (u & 0xFFFFFFFFFFFFFULL)));
+        const double d = __ll2double_rn(v);
+        const int hi = __double2hiint(d) - (FX_SHIFT << 20);
+        return v == 0 ? 0.0 : __hiloint2double(hi, __double2loint(d));
     }
 };
 

@@ -1,8 +1,11 @@
 """Fluid health status (GPU): a fluid cell whose density of Eq. (4) is not
 finite and positive raises a status bit in the sweep that meets it, and the
 next synchronising call reports LBM_ERR_UNSTABLE -- no trap, the context stays
-usable.  Covered: a bulk cell (coupling-free sweep, every storage mode) and a
-cell next to a sphere (PSM weighted collision, MEM link pull)."""
+usable.  Covered: a bulk cell (coupling-free sweep, every storage mode) whose
+populations are all NaN or all negative, and a cell next to a sphere (PSM
+weighted collision, MEM link pull).  (The fixed-point collision holds no NaN:
+its conversion turns a non-finite population into 0, so a cell of NaNs
+reaches it as density 0, which the test reports.)"""
 import numpy as np
 import pytest
 
@@ -36,7 +39,7 @@ def test_bad_bulk_cell_is_reported(storage, bad):
     f = sim.pdf_f64()
     z, y, x = 3, 5, 7  # far from the sphere (centre at height 24)
     if bad == "nan":
-        f[4, z, y, x] = np.nan
+        f[:, z, y, x] = np.nan
     else:
         f[:, z, y, x] = -np.abs(f[:, z, y, x])
     sim.set_pdf_pre(f)
