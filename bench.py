@@ -244,6 +244,7 @@ def run_learned(args, stream):
         "speedup_vs_fine_fp64": res["speedup_vs_fine_fp64"],
         "training_loss": [res["loss_history"][0], res["loss_history"][-1]],
         "samples": res["samples"], "coarse_steps": res["coarse_steps"],
+        "train_steps": res["train_steps"], "train_ms_per_step": res["train_ms_per_step"],
     }
 
 

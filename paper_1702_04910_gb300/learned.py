@@ -108,7 +108,8 @@ def teacher_forced(case_c, fine_rec, ratio: int, stream=None, storage: str = "f6
 def train(X: np.ndarray, Y: np.ndarray, steps: int = 2000, lr: float = 1e-3, seed: int = 0,
           stream=None):
     """Fits the normalisation and trains the network on the GPU; returns the
-    model and the loss history (every 100 steps)."""
+    model, the loss history (every 100 steps) and the device time of one
+    full-batch training step (ms, CUDA events around the Adam steps)."""
     import torch
 
     dev = torch.device("cuda")
@@ -119,13 +120,19 @@ def train(X: np.ndarray, Y: np.ndarray, steps: int = 2000, lr: float = 1e-3, see
     m.fit_normalization(x.data_ptr(), t.data_ptr(), x.shape[0])
     hist = []
     done = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
     while done < steps:
         k = min(100, steps - done)
+        ev0.record()
         hist.append(m.train(x.data_ptr(), t.data_ptr(), x.shape[0], k, lr))
+        ev1.record()
+        ev1.synchronize()
+        ms += ev0.elapsed_time(ev1)
         done += k
     _, final = m.gradient(x.data_ptr(), t.data_ptr(), x.shape[0])
     hist.append(final)
-    return m, hist
+    return m, hist, ms / max(steps, 1)
 
 
 def init_params(seed: int) -> np.ndarray:
@@ -204,7 +211,7 @@ def experiment(train_ga, test_ga, coupling="PSM_M2B2", D_c=12.0, ratio=4, u_ref=
         Ys.append(Y)
     X = np.concatenate(Xs)
     Y = np.concatenate(Ys)
-    model, hist = train(X, Y, train_steps, lr, seed, stream)
+    model, hist, train_ms = train(X, Y, train_steps, lr, seed, stream)
     if log:
         log(f"trained on {X.shape[0]} samples: loss {hist[0]:.4g} -> {hist[-1]:.4g}")
     K = fine_steps // ratio
@@ -228,6 +235,7 @@ def experiment(train_ga, test_ga, coupling="PSM_M2B2", D_c=12.0, ratio=4, u_ref=
         "coarse_storage": coarse_storage, "fine_storage": "f64",
         "fine_steps": fine_steps, "coarse_steps": K, "train_ga": list(train_ga),
         "test_ga": list(test_ga), "samples": int(X.shape[0]), "loss_history": hist,
+        "train_steps": train_steps, "train_ms_per_step": train_ms,
         "cases": results,
         # time of one settling run: fine (per case share of the batched FP64
         # run) against the corrected coarse run of the same physical duration
