@@ -17,8 +17,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 #include "lbm_fixed.cuh"
 
 namespace lbmgpu {
@@ -333,21 +331,12 @@ __device__ __forceinline__ long long lin(const Geom& g, int x, int y, int z) {
 template <typename T>
 struct PdfStore {
     template <typename C>
-    __device__ __forceinline__ static C load(const T* p, int q) {
-        if constexpr (std::is_same<C, fx64>::value && std::is_same<T, double>::value) {
-            const double d = __ldg(p);
-            return q < FX_INT_LOADS ? fx64(fx64::from_double_int(d), 0) : fx64(d);
-        } else {
-            return (C)__ldg(p);
-        }
+    __device__ __forceinline__ static C load(const T* p, int) {
+        return (C)__ldg(p);
     }
     template <typename C>
-    __device__ __forceinline__ static T save(C v, int q) {
-        if constexpr (std::is_same<C, fx64>::value && std::is_same<T, double>::value) {
-            return q < FX_INT_STORES ? fx64::to_double_int(v.v) : (T)v;
-        } else {
-            return (T)v;
-        }
+    __device__ __forceinline__ static T save(C v, int) {
+        return (T)v;
     }
 };
 template <>

@@ -58,54 +58,7 @@ struct fx64 {
         const int hi = __double2hiint(d) - (FX_SHIFT << 20);
         return v == 0 ? 0.0 : __hiloint2double(hi, __double2loint(d));
     }
-
-    // The same conversions on the integer pipes alone (the hardware ones
-    // above run on the FP64 pipe): the 53-bit significand shifted by the
-    // exponent (truncating), and a normalisation by a leading-zero count
-    // (rounding to nearest, ties away from zero).  A sweep may convert some
-    // directions this way to balance the two pipes (FX_INT_LOADS / _STORES).
-    __device__ static __forceinline__ long long from_double_int(double d) {
-        const long long b = __double_as_longlong(d);
-        const int e = (int)((b >> 52) & 0x7FF);
-        const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-        const int sh = e - (1075 - FX_SHIFT);  // x 2^58 = m 2^sh
-        long long r;
-        if (e == 0)
-            r = 0;
-        else if (sh >= 0)
-            r = sh < 10 ? (m << sh) : 0x7FFFFFFFFFFFFFFFLL;
-        else
-            r = sh > -63 ? (m >> (-sh)) : 0;
-        return b < 0 ? -r : r;
-    }
-
-    __device__ static __forceinline__ double to_double_int(long long v) {
-        if (v == 0) return 0.0;
-        const unsigned long long sgn = v < 0 ? (1ULL << 63) : 0ULL;
-        unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-        int p = 63 - __clzll((long long)u);  // top bit: value in [2^(p-58), 2^(p-57))
-        if (p > 52) {
-            u += 1ULL << (p - 53);  // round to nearest (ties away from zero)
-            if (u >> (p + 1)) ++p;  // carried into a new top bit
-            u >>= (p - 52);
-        } else {
-            u <<= (52 - p);
-        }
-        const unsigned long long e = (unsigned long long)(p - FX_SHIFT + 1023);
-        return __longlong_as_double((long long)(sgn | (e << 52) | (u & 0xFFFFFFFFFFFFFULL)));
-    }
 };
-
-// Directions q < FX_INT_LOADS (FX_INT_STORES) of the fixed-point sweep convert
-// on the integer pipes, the others with the hardware conversion.
-#ifndef LBM_FX_INT_LOADS
-#define LBM_FX_INT_LOADS 0
-#endif
-#ifndef LBM_FX_INT_STORES
-#define LBM_FX_INT_STORES 0
-#endif
-constexpr int FX_INT_LOADS = LBM_FX_INT_LOADS;
-constexpr int FX_INT_STORES = LBM_FX_INT_STORES;
 
 __device__ __forceinline__ fx64 operator+(fx64 a, fx64 b) { return fx64(a.v + b.v, 0); }
 __device__ __forceinline__ fx64 operator-(fx64 a, fx64 b) { return fx64(a.v - b.v, 0); }

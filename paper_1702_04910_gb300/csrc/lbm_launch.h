@@ -209,9 +209,10 @@ enum : int {
     ST_BOUNDS = 16,           // an index check in a coupling kernel failed (access skipped)
     ST_FLUID = 32,            // a fluid cell's density became non-finite or <= 0
 };
-static_assert(ST_TOO_MANY_OBJECTS == LBM_STATUS_TOO_MANY_OBJECTS && ST_DOMAIN == LBM_STATUS_DOMAIN &&
-                  ST_UNSTABLE == LBM_STATUS_UNSTABLE && ST_BOUNDS == LBM_STATUS_BOUNDS &&
-                  ST_FLUID == LBM_STATUS_FLUID,
+static_assert((int)ST_TOO_MANY_OBJECTS == (int)LBM_STATUS_TOO_MANY_OBJECTS &&
+                  (int)ST_DOMAIN == (int)LBM_STATUS_DOMAIN &&
+                  (int)ST_UNSTABLE == (int)LBM_STATUS_UNSTABLE &&
+                  (int)ST_BOUNDS == (int)LBM_STATUS_BOUNDS && (int)ST_FLUID == (int)LBM_STATUS_FLUID,
               "status bits of the public header");
 
 // storage: 0 = FP64, 1 = FP32 (arithmetic in the same precision), 4 = FP16

@@ -85,6 +85,28 @@ def test_batch_matches_oracle_per_case(storage):
         o.close()
 
 
+def test_batch_psm_with_two_subcycles():
+    """PSM cases with the two averaged LBM subcycles of Sec. 4.1 (R30) beside
+    one-sweep PSM and MEM cases in one batch: a free M3B2 sphere (stable with
+    the averaged force) and a free M2B2 one, each against its oracle run."""
+    from paper_1702_04910_gb300.binding import Batch
+    cases = W.ensemble(4, seed=5, d_range=(5, 7),
+                       couplings=("PSM_M3B2", "PSM_M2B2", "PSM_M1B1", "MEM_CLI"))
+    cases[0]["subcycles"] = 2
+    cases[1]["subcycles"] = 2
+    steps = 10
+    b = Batch(cases)
+    assert b.cell_updates == sum(int(np.prod(c["shape"])) * c["subcycles"] for c in cases)
+    b.step(steps)
+    pdfs, F, T, parts = batch_state(b)
+    b.close()
+    for c, case in enumerate(cases):
+        o = oracle_run(case, steps)
+        check_case(o, case, pdfs[c], F[c], T[c], parts[c])
+        assert np.all(np.isfinite(parts[c]["u"]))
+        o.close()
+
+
 def test_batch_tilings_and_autotune_are_bitwise_neutral():
     from paper_1702_04910_gb300.binding import Batch
     cases = small_ensemble(seed=11)
