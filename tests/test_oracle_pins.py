@@ -244,16 +244,18 @@ def test_uniform_translation_is_force_free(lattice, coupling):
 
 @pytest.mark.parametrize("coupling", ["PSM_M1B1", "PSM_M2B2", "PSM_M3B2"])
 @pytest.mark.parametrize("subcycles", [1, 2])
-def test_psm_momentum_balance(lattice, coupling, subcycles):
+@pytest.mark.parametrize("collision", ["BGK", "TRT"])
+def test_psm_momentum_balance(lattice, coupling, subcycles, collision):
     """Momentum of a periodic box changes per sweep by sum (1-B) f_ext minus
     the PSM force Eq. (28): the solid term is the only exchange with the
-    sphere.  With two subcycles (Sec. 4.1) the step reports the mean force of
+    sphere, whether the fluid part of Eq. (20) is BGK (as printed) or TRT
+    (R3).  With two subcycles (Sec. 4.1) the step reports the mean force of
     its two sweeps."""
     c, w, _ = lattice
     shape = (14, 13, 12)
     tau = 0.9
     fext = np.array([2e-5, 1e-5, -1e-5])
-    o = Oracle(shape, coupling=coupling, collision="BGK", tau=tau, fext=fext,
+    o = Oracle(shape, coupling=coupling, collision=collision, tau=tau, fext=fext,
                subcycles=subcycles)
     o.set_particles([{"x": (6.9, 6.3, 5.8), "u": (0.01, 0, -0.02), "omega": (0, 0.003, 0.001),
                       "diameter": 6.2, "fixed": 1}])
@@ -269,6 +271,35 @@ def test_psm_momentum_balance(lattice, coupling, subcycles):
     expect = subcycles * (fext * (1.0 - B).sum() - F[0])
     assert np.allclose(dJ, expect, atol=1e-13)
     assert np.max(np.abs(F)) > 1e-4  # the exchange is not trivially zero
+
+
+@pytest.mark.parametrize("coupling", ["PSM_M1B1", "PSM_M2B2", "PSM_M3B2"])
+@pytest.mark.parametrize("collision", ["BGK", "TRT"])
+def test_psm_without_solid_is_the_fluid_collision(lattice, coupling, collision):
+    """Eq. (26) with B = 0 is the plain fluid update of Eq. (1): cells that no
+    sphere reaches, and whose neighbours no sphere reaches either, end the
+    step exactly as in a run without coupling (BGK or TRT fluid part)."""
+    c, w, _ = lattice
+    shape = (16, 14, 12)
+    kw = dict(collision=collision, tau=0.8, fext=(1e-5, -2e-5, 3e-6))
+    f0 = W.perturbed_field(w, shape, 0.04, seed=13)
+    psm = Oracle(shape, coupling=coupling, **kw)
+    psm.set_particles([{"x": (5.1, 6.7, 5.9), "u": (0.01, -0.02, 0.0), "diameter": 5.0,
+                        "fixed": 1}])
+    free = Oracle(shape, coupling="NONE", **kw)
+    eps = psm.eps(0)
+    psm.set_pdf(f0)
+    free.set_pdf(f0)
+    psm.step(1)
+    free.step(1)
+    touched = eps > 0
+    near = touched.copy()
+    for cq in c[1:]:  # one step of streaming reach along every lattice link
+        near |= np.roll(touched, tuple(int(v) for v in cq[::-1]), axis=(0, 1, 2))
+    far = ~near
+    assert far.sum() > 1000 and touched.sum() > 50
+    assert np.array_equal(psm.pdf("pre")[:, far], free.pdf("pre")[:, far])
+    assert not np.array_equal(psm.pdf("pre")[:, touched], free.pdf("pre")[:, touched])
 
 
 @pytest.mark.parametrize("coupling", ["MEM_BB", "MEM_CLI", "MEM_MR"])
