@@ -635,65 +635,46 @@ struct PullPair<T, NQ> {
 
 // Grid (ceil(nx / (2 PAIR_TX)), ceil(ny / PAIR_TY), nz), block (PAIR_TX, PAIR_TY).
 constexpr int PAIR_TX = 64, PAIR_TY = 4;
-// z planes per thread (all their loads are issued before the first collision)
-#ifndef LBM_PAIR_ZP
-#define LBM_PAIR_ZP 1
-#endif
-constexpr int PAIR_ZP = LBM_PAIR_ZP;
 
-template <typename T, int ZP>
-__global__ void __launch_bounds__(PAIR_TX * PAIR_TY, ZP == 1 ? 3 : 2)
+template <typename T>
+__global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
     k_bulk_pair(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<float> k,
                 const DevParticle* __restrict__ parts, int np, int* __restrict__ status) {
     const int bx0 = 2 * blockIdx.x * PAIR_TX, by0 = blockIdx.y * PAIR_TY;
     const int x0 = bx0 + 2 * threadIdx.x;
-    const int y = by0 + threadIdx.y, z0 = blockIdx.z * ZP;
+    const int y = by0 + threadIdx.y, z = blockIdx.z;
     if (x0 >= g.nx || y >= g.ny) return;
+    // k_near's cells are left alone; a block whose cells no region reaches
+    // (block-uniform test) skips the per-cell one
+    bool near_a = false, near_b = false;
+    for (int s = 0; s < np; ++s) {
+        const int* r = parts[s].reg;
+        if (!in_range(z, r[8], r[9], g.nz) ||
+            !spans_meet(by0, min(PAIR_TY, g.ny - by0), r[4], r[5], g.ny) ||
+            !spans_meet(bx0, min(2 * PAIR_TX, g.nx - bx0), r[0], r[1], g.nx))
+            continue;
+        near_a = near_a || cell_in_reg(g, r, x0, y, z);
+        near_b = near_b || cell_in_reg(g, r, x0 + 1, y, z);
+    }
+    if (near_a && near_b) return;
+    const NbrOff o = make_off(g, x0, y, z);
+    const long long row = lin(g, 0, y, z);
     const int xm2 = x0 == 0 ? g.nx - 2 : x0 - 2;
     const int xp2 = x0 + 2 == g.nx ? 0 : x0 + 2;
-    float fa[ZP][NQ], fb[ZP][NQ];
-    bool near_a[ZP], near_b[ZP], act[ZP];
+    float fa[NQ], fb[NQ];
+    PullPair<T, 0>::run(src, g, o, row, x0, xm2, xp2, fa, fb);
+    const bool bad_a = collide_fluid<float, true>(fa, k), bad_b = collide_fluid<float, true>(fb, k);
+    if ((bad_a && !near_a) || (bad_b && !near_b)) atomicOr(status, ST_FLUID);
+    if (!near_a && !near_b) {
 #pragma unroll
-    for (int p = 0; p < ZP; ++p) {
-        const int z = z0 + p;
-        act[p] = z < g.nz;
-        // k_near's cells are left alone; a block whose cells no region
-        // reaches (block-uniform test) skips the per-cell one
-        near_a[p] = false;
-        near_b[p] = false;
-        for (int s = 0; act[p] && s < np; ++s) {
-            const int* r = parts[s].reg;
-            if (!in_range(z, r[8], r[9], g.nz) ||
-                !spans_meet(by0, min(PAIR_TY, g.ny - by0), r[4], r[5], g.ny) ||
-                !spans_meet(bx0, min(2 * PAIR_TX, g.nx - bx0), r[0], r[1], g.nx))
-                continue;
-            near_a[p] = near_a[p] || cell_in_reg(g, r, x0, y, z);
-            near_b[p] = near_b[p] || cell_in_reg(g, r, x0 + 1, y, z);
-        }
-        act[p] = act[p] && !(near_a[p] && near_b[p]);
-        if (act[p]) {
-            const NbrOff o = make_off(g, x0, y, z);
-            PullPair<T, 0>::run(src, g, o, lin(g, 0, y, z), x0, xm2, xp2, fa[p], fb[p]);
-        }
-    }
+        for (int q = 0; q < NQ; ++q)
+            *reinterpret_cast<unsigned*>(dst + (long long)q * g.n + row + x0) =
+                Pair16<T>::pack(fa[q], fb[q]);
+    } else {
+        const long long idx = row + x0 + (near_a ? 1 : 0);
+        const float(&f)[NQ] = near_a ? fb : fa;
 #pragma unroll
-    for (int p = 0; p < ZP; ++p) {
-        if (!act[p]) continue;
-        const long long row = lin(g, 0, y, z0 + p);
-        const bool bad_a = collide_fluid<float, true>(fa[p], k);
-        const bool bad_b = collide_fluid<float, true>(fb[p], k);
-        if ((bad_a && !near_a[p]) || (bad_b && !near_b[p])) atomicOr(status, ST_FLUID);
-        if (!near_a[p] && !near_b[p]) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q)
-                *reinterpret_cast<unsigned*>(dst + (long long)q * g.n + row + x0) =
-                    Pair16<T>::pack(fa[p][q], fb[p][q]);
-        } else {
-            const long long idx = row + x0 + (near_a[p] ? 1 : 0);
-            const float(&f)[NQ] = near_a[p] ? fb[p] : fa[p];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + idx] = Pair16<T>::one(f[q]);
-        }
+        for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + idx] = Pair16<T>::one(f[q]);
     }
 }
 
@@ -1626,8 +1607,8 @@ cudaError_t bulk_t(const void* src, void* dst, const Launch& L) {
         // no open boundaries (those planes take the per-cell kernel)
         if (!L.nostream && L.g.nx % 2 == 0 && L.g.bc_z != 2) {
             dim3 grid((L.g.nx + 2 * PAIR_TX - 1) / (2 * PAIR_TX), (L.g.ny + PAIR_TY - 1) / PAIR_TY,
-                      (L.g.nz + PAIR_ZP - 1) / PAIR_ZP);
-            k_bulk_pair<T, PAIR_ZP><<<grid, dim3(PAIR_TX, PAIR_TY, 1), 0, L.stream>>>(
+                      L.g.nz);
+            k_bulk_pair<T><<<grid, dim3(PAIR_TX, PAIR_TY, 1), 0, L.stream>>>(
                 (const T*)src, (T*)dst, L.g, L.kf, L.parts, L.all_tiles ? 0 : L.cp.np, L.status);
             return cudaGetLastError();
         }
