@@ -283,6 +283,52 @@ def run_frame_study(args):
                       "shape": frame.frame_shape(args.frame), "results": out}), flush=True)
 
 
+def run_full_settling(args):
+    """The settling workload for its full length: every coupling released at
+    rest and run for --full-steps global steps (MEM: two sweeps each) in
+    --full-storage, the sphere's height and vertical velocity sampled every
+    100 steps, the first step at which it rests on the bottom wall (wall
+    contact keeps it one cell off, R13) and where a run became unstable."""
+    import numpy as np
+    import torch
+
+    from paper_1702_04910_gb300 import workloads as W
+    from paper_1702_04910_gb300.binding import LbmError, Simulation
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for cp in args.couplings:
+        case = workload(cp, args.scale)
+        s = Simulation(case["shape"], stream=stream, storage=args.full_storage,
+                       **W.sim_kwargs(case))
+        s.set_particles(case["particles"])
+        s.init_equilibrium()
+        R = 0.5 * case["particles"][0]["diameter"]
+        samples, contact, failed = [], None, None
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.full_steps:
+            n = min(100, args.full_steps - done)
+            s.step(n)
+            done += n
+            try:
+                p = s.get_particles()[0]
+            except LbmError as e:
+                failed = f"{e} (within global steps {done - n}..{done})"
+                break
+            samples.append([done, round(float(p["x"][2]), 3), round(float(p["u"][2]), 6)])
+            if contact is None and p["x"][2] - R <= 1.0 + 1e-9:
+                contact = done
+        s.close()
+        uz = np.array([v[2] for v in samples]) if samples else np.zeros(0)
+        out[cp] = {"steps_run": done, "lattice_time": done * sweeps_of(cp), "failed": failed,
+                   "wall_contact_step": contact,
+                   "max_settling_speed": float(-uz.min()) if uz.size else None,
+                   "seconds": time.perf_counter() - t0, "samples_every_100_steps": samples}
+    print(json.dumps({"full_settling": WORKLOAD, "steps": args.full_steps,
+                      "storage": args.full_storage, "results": out}), flush=True)
+
+
 def run_lab_drag(args):
     """Drag of a sphere moving relative to the fluid at the same speed in two
     frames: (A) held fixed in the open frame of Sec. 4.1 with a uniform inflow
@@ -798,6 +844,12 @@ def main():
                     help="drag of a fixed sphere in an inflow against a sphere translating "
                          "through fluid at rest at the same relative speed (D = 24)")
     ap.add_argument("--lab-drag-windows", type=int, default=60)
+    ap.add_argument("--full-settling", action="store_true",
+                    help="run the settling workload for --full-steps global steps per coupling "
+                         "and report wall contact and stability")
+    ap.add_argument("--full-steps", type=int, default=20000)
+    ap.add_argument("--full-storage", default="f64fx",
+                    choices=("f64", "f64fx", "f64ff", "f32", "f16s", "bf16s"))
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the settling workload by this factor in every length (tests)")
     ap.add_argument("--case-shape", default=None,
@@ -817,6 +869,8 @@ def main():
         run_case(args)
     elif args.lab_drag and args.impl == "ours":
         run_lab_drag(args)
+    elif args.full_settling and args.impl == "ours":
+        run_full_settling(args)
     elif args.ensemble_only and args.impl == "ours":
         run_ensemble_only(args)
     elif args.frame is not None and args.impl == "ours":
