@@ -547,20 +547,22 @@ __device__ __forceinline__ void moments_j(const C (&f)[NQ], C& rho, C& jx, C& jy
 //   f_q' = hs (f_q + f_qbar) + hd (f_q - f_qbar) - (P + M),
 //   f_qbar' = hs (f_q + f_qbar) - hd (f_q - f_qbar) - (P - M):
 // two products per pair instead of four (PairSumDiff, lbm_fixed.cuh).
-template <typename C, int Q, int K, bool FORCE>
-__device__ __forceinline__ void trt_pair(C (&f)[NQ], C cu, const C (&bw)[3], const Coll<C>& k) {
+// C is the arithmetic type, KT the type of the constants (C itself, or float
+// for the packed f2: C(k.x) broadcasts a constant to both lanes).
+template <typename C, int Q, int K, bool FORCE, typename KT>
+__device__ __forceinline__ void trt_pair(C (&f)[NQ], C cu, const C (&bw)[3], const Coll<KT>& k) {
     constexpr int QB = Q + 1;
-    C P = FORCE ? fma(k.k1w[K], cu * cu, fma(-k.gq[(Q - 1) / 2], cu, bw[K]))
-                : fma(k.k1w[K], cu * cu, bw[K]);
-    C M = FORCE ? fma(k.k2w[K], cu, -k.fq[(Q - 1) / 2]) : k.k2w[K] * cu;
+    C P = FORCE ? fma(C(k.k1w[K]), cu * cu, fma(C(-k.gq[(Q - 1) / 2]), cu, bw[K]))
+                : fma(C(k.k1w[K]), cu * cu, bw[K]);
+    C M = FORCE ? fma(C(k.k2w[K]), cu, C(-k.fq[(Q - 1) / 2])) : C(k.k2w[K]) * cu;
     const C a = f[Q], b = f[QB];
     if constexpr (PairSumDiff<C>::value) {
         const C sp = k.hs * (a + b), sd = k.hd * (a - b);
         f[Q] = (sp + sd) - (P + M);
         f[QB] = (sp - sd) - (P - M);
     } else {
-        f[Q] = fma(k.alpha, a, fma(k.beta, b, -(P + M)));
-        f[QB] = fma(k.alpha, b, fma(k.beta, a, -(P - M)));
+        f[Q] = fma(C(k.alpha), a, fma(C(k.beta), b, -(P + M)));
+        f[QB] = fma(C(k.alpha), b, fma(C(k.beta), a, -(P - M)));
     }
 }
 
@@ -575,6 +577,22 @@ __device__ __forceinline__ void trt_pair_sd(C (&f)[NQ], C cu, C P, const Coll<C>
     f[QB] = (sp - sd) - (P - M);
 }
 
+// Two FP32 lanes in one register pair, for the Blackwell packed f32x2
+// add / multiply / FMA (one instruction for both lanes, each lane rounded as
+// the scalar operation).  The 16-bit pair sweep keeps its two cells in the two
+// lanes; constants are broadcast with f2(c).
+struct f2 {
+    float2 v;
+    __device__ __forceinline__ f2() {}
+    __device__ __forceinline__ explicit f2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ explicit f2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__fadd2_rn(a.v, (-b).v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+
 // Fluid health: the density of Eq. (4) of a cell must be finite and
 // positive.  Bit tests on the integer pipes (no FP64 instruction): a value
 // outside (0, +inf) -- zero, negative, infinite or NaN -- is reported.  (The
@@ -585,6 +603,10 @@ __device__ __forceinline__ bool density_bad(double r) {
 }
 __device__ __forceinline__ bool density_bad(float r) {
     return __float_as_uint(r) - 1u >= 0x7F7FFFFFu;
+}
+// packed pair: bit 0 for lane x, bit 1 for lane y
+__device__ __forceinline__ unsigned density_bad(f2 r) {
+    return (density_bad(r.v.x) ? 1u : 0u) | (density_bad(r.v.y) ? 2u : 0u);
 }
 // fixed point cannot hold NaN (the conversion from FP64 turns a non-finite
 // value into 0); a saturated conversion or a wrapped sum shows as a density
@@ -597,11 +619,13 @@ __device__ __forceinline__ bool density_bad(fx64 r) {
 // SHIFTED: f holds the shifted populations f_q - w_q, whose sum is rho - 1.
 // Written in j = rho0 U (ux, uy, uz below hold j); the constants k1w, k2w,
 // m15r0, hw and gq carry the powers of 1/rho0 that U would bring.
-template <typename C, bool FORCE, bool SHIFTED>
-__device__ __forceinline__ bool collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
+// KT: type of the constants (see trt_pair).  The result is density_bad's:
+// a bool, or a lane mask for the packed f2.
+template <typename C, bool FORCE, bool SHIFTED, typename KT>
+__device__ __forceinline__ auto collide_fluid_t(C (&f)[NQ], const Coll<KT>& k) {
     C rho, ux, uy, uz;
     moments_j(f, rho, ux, uy, uz);
-    const bool bad = SHIFTED ? density_bad(rho + (C)1) : density_bad(rho);
+    const auto bad = SHIFTED ? density_bad(rho + C(1)) : density_bad(rho);
     if constexpr (PairSumDiff<C>::value && !FORCE) {
         // products shared between pairs: with t_a = k1w_diag u_a^2 and
         // c_ab = k1w_axis u_a u_b (k1w_axis = 2 k1w_diag), the quadratic term
@@ -626,17 +650,17 @@ __device__ __forceinline__ bool collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
         return bad;
     }
     const C uu = fma(ux, ux, fma(uy, uy, uz * uz));
-    const C base = fma(k.m15r0, uu, rho);
+    const C base = fma(C(k.m15r0), uu, rho);
     C bw[3];
     if (FORCE) {
-        const C uf = fma(ux, k.fx, fma(uy, k.fy, uz * k.fz));
+        const C uf = fma(ux, C(k.fx), fma(uy, C(k.fy), uz * C(k.fz)));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) bw[c] = fma(k.lpw[c], base, k.hw[c] * uf);
+        for (int c = 0; c < 3; ++c) bw[c] = fma(C(k.lpw[c]), base, C(k.hw[c]) * uf);
     } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) bw[c] = k.lpw[c] * base;
+        for (int c = 0; c < 3; ++c) bw[c] = C(k.lpw[c]) * base;
     }
-    f[0] = fma(k.c0, f[0], -bw[0]);
+    f[0] = fma(C(k.c0), f[0], -bw[0]);
     trt_pair<C, 1, 1, FORCE>(f, ux, bw, k);
     trt_pair<C, 3, 1, FORCE>(f, uy, bw, k);
     trt_pair<C, 5, 1, FORCE>(f, uz, bw, k);
@@ -653,8 +677,8 @@ __device__ __forceinline__ bool collide_fluid_t(C (&f)[NQ], const Coll<C>& k) {
 // and forcing Eq. (7), in place.  Returns true when the cell's density is
 // not finite and positive (density_bad).  SHIFTED: f holds f_q - w_q (the
 // 16-bit storage's populations, collided as they are).
-template <typename C, bool SHIFTED = false>
-__device__ __forceinline__ bool collide_fluid(C (&f)[NQ], const Coll<C>& k) {
+template <typename C, bool SHIFTED = false, typename KT>
+__device__ __forceinline__ auto collide_fluid(C (&f)[NQ], const Coll<KT>& k) {
     if (k.has_force) return collide_fluid_t<C, true, SHIFTED>(f, k);
     return collide_fluid_t<C, false, SHIFTED>(f, k);
 }

@@ -594,7 +594,7 @@ __device__ __forceinline__ unsigned ld_word(const void* p) {
 template <typename T, int Q>
 __device__ __forceinline__ void pull_pair_one(const T* __restrict__ src, const Geom& g,
                                               const NbrOff& o, long long row, int x0, int xm2,
-                                              int xp2, float (&fa)[NQ], float (&fb)[NQ]) {
+                                              int xp2, f2 (&f)[NQ]) {
     float2 v;
     if ((cz(Q) > 0 && o.zlo) || (cz(Q) < 0 && o.zhi)) {
         v = Pair16<T>::unpack(ld_word(src + (long long)opp(Q) * g.n + row + x0));  // halfway BB
@@ -613,24 +613,22 @@ __device__ __forceinline__ void pull_pair_one(const T* __restrict__ src, const G
             v = Pair16<T>::unpack(__byte_perm(ld_word(a + x0), ld_word(a + xp2), 0x5432));
         }
     }
-    fa[Q] = v.x;  // shifted values g_q (see above)
-    fb[Q] = v.y;
+    f[Q] = f2(v);  // shifted values g_q (see above), cell x0 in lane x
 }
 
 template <typename T, int Q>
 struct PullPair {
     __device__ __forceinline__ static void run(const T* __restrict__ src, const Geom& g,
                                                const NbrOff& o, long long row, int x0, int xm2,
-                                               int xp2, float (&fa)[NQ], float (&fb)[NQ]) {
-        pull_pair_one<T, Q>(src, g, o, row, x0, xm2, xp2, fa, fb);
-        PullPair<T, Q + 1>::run(src, g, o, row, x0, xm2, xp2, fa, fb);
+                                               int xp2, f2 (&f)[NQ]) {
+        pull_pair_one<T, Q>(src, g, o, row, x0, xm2, xp2, f);
+        PullPair<T, Q + 1>::run(src, g, o, row, x0, xm2, xp2, f);
     }
 };
 template <typename T>
 struct PullPair<T, NQ> {
     __device__ __forceinline__ static void run(const T* __restrict__, const Geom&, const NbrOff&,
-                                               long long, int, int, int, float (&)[NQ],
-                                               float (&)[NQ]) {}
+                                               long long, int, int, int, f2 (&)[NQ]) {}
 };
 
 // Grid (ceil(nx / (2 PAIR_TX)), ceil(ny / PAIR_TY), nz), block (PAIR_TX, PAIR_TY).
@@ -661,20 +659,21 @@ __global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
     const long long row = lin(g, 0, y, z);
     const int xm2 = x0 == 0 ? g.nx - 2 : x0 - 2;
     const int xp2 = x0 + 2 == g.nx ? 0 : x0 + 2;
-    float fa[NQ], fb[NQ];
-    PullPair<T, 0>::run(src, g, o, row, x0, xm2, xp2, fa, fb);
-    const bool bad_a = collide_fluid<float, true>(fa, k), bad_b = collide_fluid<float, true>(fb, k);
-    if ((bad_a && !near_a) || (bad_b && !near_b)) atomicOr(status, ST_FLUID);
+    // both cells collide in the two lanes of the packed f32x2 arithmetic
+    f2 f[NQ];
+    PullPair<T, 0>::run(src, g, o, row, x0, xm2, xp2, f);
+    const unsigned bad = collide_fluid<f2, true>(f, k);
+    if (((bad & 1u) && !near_a) || ((bad & 2u) && !near_b)) atomicOr(status, ST_FLUID);
     if (!near_a && !near_b) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
             *reinterpret_cast<unsigned*>(dst + (long long)q * g.n + row + x0) =
-                Pair16<T>::pack(fa[q], fb[q]);
+                Pair16<T>::pack(f[q].v.x, f[q].v.y);
     } else {
         const long long idx = row + x0 + (near_a ? 1 : 0);
-        const float(&f)[NQ] = near_a ? fb : fa;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) dst[(long long)q * g.n + idx] = Pair16<T>::one(f[q]);
+        for (int q = 0; q < NQ; ++q)
+            dst[(long long)q * g.n + idx] = Pair16<T>::one(near_a ? f[q].v.y : f[q].v.x);
     }
 }
 
