@@ -90,6 +90,17 @@
  *      + 2 f_eq,+_q(rho_out, u(x,t)), with f_eq,+ the even part of Eq. (3)
  *      and u(x,t) the velocity of Eq. (8) of the boundary cell before the
  *      stream.
+ * R32  Re-mapping momentum (optional, remap_charge = 1; Algorithm 1 has no
+ *      such step, so the default is 0).  The re-mapping at the end of a MEM
+ *      step removes from the fluid the momentum sum_q c_q f_q of every cell
+ *      the particle covers and creates that of every cell it uncovers (after
+ *      the refill of Eq. (19)).  With the option on, the difference dP
+ *      (created minus removed) and its moment dL about the particle's new
+ *      centre (arm x_c - X_p) are kept, and the next step's averaged force
+ *      and torque become F - dP/dt and T - dL/dt, dt the step's lattice time
+ *      (the LBM subcycles), before the rigid-body update: the particle then
+ *      gives or takes what the fluid gained or lost.  Replacing particles
+ *      from the host clears the pending amounts.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -132,6 +143,7 @@ typedef struct {
     int wall_contact;  /* R13 */
     double inflow[3];  /* bc_z = 2: inflow velocity at z = 0 (R27) */
     double rho_out;    /* bc_z = 2: outflow density at z = nz (R27) */
+    int remap_charge;  /* MEM: charge the re-mapping momentum (R32) */
 } orc_params;
 
 typedef struct {
@@ -153,6 +165,8 @@ typedef struct {
     double *eps;         /* PSM: eps_s per cell, [s][cell] for current P */
     double *force, *torque; /* last hydrodynamic force / torque, [s][3] */
     double *fsum, *tsum;    /* per-subcycle accumulators */
+    double *charge;         /* R32: momentum / angular momentum the last
+                               re-mapping gave the fluid, [s][6] */
     long steps;
 } orc_sim;
 
@@ -669,11 +683,43 @@ static int rigid_body_update(orc_sim *s, double dt) {
 }
 
 /* ---- MEM re-mapping and PDF reconstruction, Eq. (19), R9-R11 ------------ */
-static void remap_and_refill(orc_sim *s, int use_extrapolation) {
+/* Adds sign * (j, (x_c - X_p) x j) of cell (x, y, z) with momentum
+ * j = sum_q c_q f_q to particle P's six entries of `charge` (R32). */
+static void add_cell_momentum(const orc_sim *s, const orc_particle *P, int x, int y, int z,
+                              const double fc[NQ], double sign, double *charge) {
+    double xc[3], arm[3], j[3] = {0.0, 0.0, 0.0}, L[3];
+    for (int q = 0; q < NQ; ++q)
+        for (int a = 0; a < 3; ++a) j[a] += CQ[q][a] * fc[q];
+    cell_centre(x, y, z, xc);
+    separation(s, xc, P->x, arm);
+    cross(arm, j, L);
+    for (int a = 0; a < 3; ++a) {
+        charge[a] += sign * j[a];
+        charge[3 + a] += sign * L[a];
+    }
+}
+
+/* Re-mapping with the particle state in s->part and refilling of uncovered
+ * cells (Sec. 2.2).  charge != NULL: also the R32 amounts, [s][6]. */
+static void remap_and_refill(orc_sim *s, int use_extrapolation, double *charge) {
     int *old = s->solid;
     int *neu = (int *)malloc(sizeof(int) * (size_t)s->n);
     map_particles(s, neu);
     double rho0 = s->p.rho0;
+    if (charge) {
+        for (int k = 0; k < 6 * s->np; ++k) charge[k] = 0.0;
+        /* covered cells lose their fluid momentum (pre-collision PDFs) */
+        for (int z = 0; z < s->p.nz; ++z)
+            for (int y = 0; y < s->p.ny; ++y)
+                for (int x = 0; x < s->p.nx; ++x) {
+                    long i = cell_index(s, x, y, z);
+                    if (old[i] || !neu[i]) continue;
+                    double fc[NQ];
+                    for (int q = 0; q < NQ; ++q) fc[q] = s->f[(long)q * s->n + i];
+                    add_cell_momentum(s, &s->part[neu[i] - 1], x, y, z, fc, -1.0,
+                                      charge + 6 * (neu[i] - 1));
+                }
+    }
     for (int z = 0; z < s->p.nz; ++z)
         for (int y = 0; y < s->p.ny; ++y)
             for (int x = 0; x < s->p.nx; ++x) {
@@ -740,6 +786,7 @@ static void remap_and_refill(orc_sim *s, int use_extrapolation) {
                     for (int q = 0; q < NQ; ++q) fnew[q] = orc_feq(q, rbar, v, rho0);
                 }
                 for (int q = 0; q < NQ; ++q) s->f[(long)q * s->n + i] = fnew[q];
+                if (charge) add_cell_momentum(s, P, x, y, z, fnew, 1.0, charge + 6 * (old[i] - 1));
             }
     memcpy(s->solid, neu, sizeof(int) * (size_t)s->n);
     free(neu);
@@ -772,7 +819,7 @@ orc_sim *orc_create(const orc_params *p) {
 void orc_destroy(orc_sim *s) {
     if (!s) return;
     free(s->f); free(s->ft); free(s->solid); free(s->part); free(s->eps);
-    free(s->force); free(s->torque); free(s->fsum); free(s->tsum);
+    free(s->force); free(s->torque); free(s->fsum); free(s->tsum); free(s->charge);
     free(s);
 }
 
@@ -793,6 +840,7 @@ int orc_set_particles(orc_sim *s, int np, const orc_particle *parts) {
     if (np != s->np) {
         if (remap) return ORC_ERR_ARG; /* particle count is fixed once mapped */
         free(s->part); free(s->eps); free(s->force); free(s->torque); free(s->fsum); free(s->tsum);
+        free(s->charge);
         s->np = np;
         s->part = (orc_particle *)calloc((size_t)(np > 0 ? np : 1), sizeof(orc_particle));
         s->eps = (double *)calloc((size_t)(np > 0 ? np : 1) * (size_t)s->n, sizeof(double));
@@ -800,10 +848,12 @@ int orc_set_particles(orc_sim *s, int np, const orc_particle *parts) {
         s->torque = (double *)calloc((size_t)(3 * (np > 0 ? np : 1)), sizeof(double));
         s->fsum = (double *)calloc((size_t)(3 * (np > 0 ? np : 1)), sizeof(double));
         s->tsum = (double *)calloc((size_t)(3 * (np > 0 ? np : 1)), sizeof(double));
+        s->charge = (double *)calloc((size_t)(6 * (np > 0 ? np : 1)), sizeof(double));
     }
+    for (int k = 0; k < 6 * np; ++k) s->charge[k] = 0.0; /* R32 */
     if (np) memcpy(s->part, parts, sizeof(orc_particle) * (size_t)np);
     if (is_mem(s->p.coupling)) {
-        if (remap) remap_and_refill(s, 0); /* R16 */
+        if (remap) remap_and_refill(s, 0, NULL); /* R16 */
         else map_particles(s, s->solid);
         s->mapped = 1;
     }
@@ -815,11 +865,17 @@ int orc_set_particles(orc_sim *s, int np, const orc_particle *parts) {
  * the particles take the given state (as after a rigid-body update) and
  * every cell they uncover is rebuilt from the current pre-collision field by
  * the same routine the MEM global step calls after its rigid-body update. */
+/* MEM test hook: give the mapped particles a new state and run the
+ * re-mapping and refill of Sec. 2.2 alone; the R32 amounts of that
+ * re-mapping become the pending charge. */
 int orc_move_and_refill(orc_sim *s, int np, const orc_particle *parts) {
     if (!is_mem(s->p.coupling) || !s->mapped || np != s->np) return ORC_ERR_ARG;
     if (np) memcpy(s->part, parts, sizeof(orc_particle) * (size_t)np);
-    remap_and_refill(s, 1);
+    remap_and_refill(s, 1, s->charge);
     return ORC_OK;
+}
+void orc_get_charge(const orc_sim *s, double *out) {
+    if (s->np > 0) memcpy(out, s->charge, sizeof(double) * 6 * (size_t)s->np);
 }
 
 int orc_get_particles(const orc_sim *s, orc_particle *out) {
@@ -952,8 +1008,14 @@ static int one_step(orc_sim *s) {
             s->force[k] = s->fsum[k] / sub;
             s->torque[k] = s->tsum[k] / sub;
         }
+        if (s->p.remap_charge) /* R32 */
+            for (int p = 0; p < np; ++p)
+                for (int a = 0; a < 3; ++a) {
+                    s->force[3 * p + a] -= s->charge[6 * p + a] / sub;
+                    s->torque[3 * p + a] -= s->charge[6 * p + 3 + a] / sub;
+                }
         int st = rigid_body_update(s, (double)sub);
-        remap_and_refill(s, 1);
+        remap_and_refill(s, 1, s->p.remap_charge ? s->charge : NULL);
         return st;
     }
     collide_fluid(s);

@@ -40,7 +40,8 @@ class Params(ct.Structure):
                 ("fext", ct.c_double * 3), ("gravity", ct.c_double * 3),
                 ("rho0", ct.c_double), ("subsample", ct.c_int),
                 ("subcycles", ct.c_int), ("wall_contact", ct.c_int),
-                ("inflow", ct.c_double * 3), ("rho_out", ct.c_double)]
+                ("inflow", ct.c_double * 3), ("rho_out", ct.c_double),
+                ("remap_charge", ct.c_int)]
 
 
 class Particle(ct.Structure):
@@ -77,6 +78,7 @@ def _load():
         lib.orc_set_particles.argtypes = [P, ct.c_int, ct.POINTER(Particle)]
         lib.orc_get_particles.argtypes = [P, ct.POINTER(Particle)]
         lib.orc_move_and_refill.argtypes = [P, ct.c_int, ct.POINTER(Particle)]
+        lib.orc_get_charge.argtypes = [P, dp]
         lib.orc_init_equilibrium.argtypes = [P, ct.c_double, dp]
         lib.orc_set_pdf.argtypes = [P, dp]
         lib.orc_step.argtypes = [P, ct.c_int]
@@ -134,7 +136,7 @@ class Oracle:
     def __init__(self, shape, *, coupling="NONE", collision="TRT", tau=0.8,
                  magic=3.0 / 16.0, fext=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0),
                  rho0=1.0, bc_z=0, subsample=4, subcycles=0, wall_contact=0,
-                 inflow=(0.0, 0.0, 0.0), rho_out=1.0):
+                 inflow=(0.0, 0.0, 0.0), rho_out=1.0, remap_charge=0):
         self._lib = _load()
         nx, ny, nz = (int(v) for v in shape)
         self.shape = (nx, ny, nz)
@@ -153,6 +155,7 @@ class Oracle:
         for a in range(3):
             p.inflow[a] = float(inflow[a])
         p.rho_out = float(rho_out)
+        p.remap_charge = int(remap_charge)
         self.params = p
         h = self._lib.orc_create(ct.byref(p))
         if not h:
@@ -204,7 +207,9 @@ class Oracle:
     def move_and_refill(self, particles):
         """MEM only: give the mapped particles a new state (as a rigid-body
         update would) and run the re-mapping and PDF reconstruction of
-        Sec. 2.2 alone on the current pre-collision field."""
+        Sec. 2.2 alone on the current pre-collision field.  The momentum
+        amounts of the re-mapping (R32) are kept as the pending charge
+        (``charge()``) whether or not the option is on."""
         st = self._lib.orc_move_and_refill(self._h, len(particles), self._records(particles))
         if st != 0:
             raise ValueError(f"oracle move_and_refill failed ({st})")
@@ -232,6 +237,15 @@ class Oracle:
     def step(self, n=1):
         st = self._lib.orc_step(self._h, int(n))
         return st
+
+    def charge(self):
+        """R32: (np, 6) momentum and angular momentum (about the new centre)
+        that the last re-mapping gave the fluid: uncovered minus covered
+        cells.  With remap_charge = 1 the next step takes charge / dt off the
+        force and torque."""
+        out = np.zeros((max(1, self.np), 6))
+        self._lib.orc_get_charge(self._h, _dp(out))
+        return out[: self.np]
 
     def forces(self):
         F = np.zeros((max(1, self.np), 3))
