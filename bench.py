@@ -301,6 +301,8 @@ def run_full_settling(args):
         case = workload(cp, args.scale)
         s = Simulation(case["shape"], stream=stream, storage=args.full_storage,
                        **W.sim_kwargs(case))
+        if args.remap_charge and cp.startswith("MEM"):
+            s.set_remap_charge(True)
         s.set_particles(case["particles"])
         s.init_equilibrium()
         R = 0.5 * case["particles"][0]["diameter"]
@@ -326,7 +328,8 @@ def run_full_settling(args):
                    "max_settling_speed": float(-uz.min()) if uz.size else None,
                    "seconds": time.perf_counter() - t0, "samples_every_100_steps": samples}
     print(json.dumps({"full_settling": WORKLOAD, "steps": args.full_steps,
-                      "storage": args.full_storage, "results": out}), flush=True)
+                      "storage": args.full_storage, "remap_charge": bool(args.remap_charge),
+                      "results": out}), flush=True)
 
 
 def run_lab_drag(args):
@@ -358,6 +361,8 @@ def run_lab_drag(args):
                                   "fixed": 1}])
             else:
                 s = Simulation((128, 128, 512), stream=stream, bc_z=0, **base)
+                if args.remap_charge and cp.startswith("MEM"):
+                    s.set_remap_charge(True)
                 s.init_equilibrium(1.0, (0.0, 0.0, 0.0))
                 s.set_particles([{"x": (64.0, 64.0, 448.0), "u": (0.0, 0.0, -U), "diameter": D,
                                   "density": 1e9, "fixed": 0}])
@@ -378,7 +383,7 @@ def run_lab_drag(args):
         out[cp] = res
     print(json.dumps({"lab_drag": "D=24, nu=0.01, relative speed 0.0744 (Ga 144: 1.24 u_ref), "
                                   f"{args.lab_drag_windows} windows of 50 global steps",
-                      "results": out}), flush=True)
+                      "remap_charge": bool(args.remap_charge), "results": out}), flush=True)
 
 
 def run_ensemble_only(args):
@@ -844,6 +849,9 @@ def main():
                     help="drag of a fixed sphere in an inflow against a sphere translating "
                          "through fluid at rest at the same relative speed (D = 24)")
     ap.add_argument("--lab-drag-windows", type=int, default=60)
+    ap.add_argument("--remap-charge", action="store_true",
+                    help="--lab-drag / --full-settling: MEM runs charge the momentum of covered "
+                         "and uncovered cells to the particle (lbm_set_remap_charge)")
     ap.add_argument("--full-settling", action="store_true",
                     help="run the settling workload for --full-steps global steps per coupling "
                          "and report wall contact and stability")

@@ -156,7 +156,10 @@ enum {
     LBM_FIELD_U = 3,       /* get only: velocity u, Eq. (8) / (27), 3*N doubles [cell][3]   */
     LBM_FIELD_EPS = 4,     /* get only: PSM solid fraction sum_s eps_s, N doubles          */
     LBM_FIELD_FLAG = 5,    /* get only: MEM owner (0 fluid, s+1 inside particle s), N int32 */
-    LBM_FIELD_PDF_F64 = 6  /* get only: the stored PDFs as FP64 values of f (shift undone) */
+    LBM_FIELD_PDF_F64 = 6, /* get only: the stored PDFs as FP64 values of f (shift undone) */
+    LBM_FIELD_REMAP_CHARGE = 7 /* MEM: the pending re-mapping momentum charge (see
+                              lbm_set_remap_charge), 6*n_particles doubles [p][Px Py Pz
+                              Lx Ly Lz]; part of a checkpoint when the charge is on */
 };
 
 /* Create a simulation.  Validates *cfg (LBM_ERR_ARG on a bad value,
@@ -188,7 +191,8 @@ lbm_status lbm_init_equilibrium(lbm_handle *h, double rho, const double u[3]);
 lbm_status lbm_step(lbm_handle *h, int nsteps);
 
 /* Hydrodynamic force and torque of the last global step, Eq. (17)-(18)
- * (MEM) or Eq. (28)-(29) (PSM), averaged over the step's subcycles.  F and T are
+ * (MEM) or Eq. (28)-(29) (PSM), averaged over the step's subcycles (MEM with
+ * lbm_set_remap_charge on: minus the pending re-mapping charge over dt).  F and T are
  * host arrays of 3*n doubles [particle][3].  Synchronises and reports any
  * device status raised since the last synchronising call. */
 lbm_status lbm_get_forces(lbm_handle *h, double *F, double *T);
@@ -202,6 +206,24 @@ lbm_status lbm_get_fields(lbm_handle *h, int what, void *dst, size_t bytes, int 
  * LBM_FIELD_PDF restores a state saved with lbm_get_fields (checkpoint);
  * LBM_FIELD_PDF_PRE sets the pre-collision PDFs at t = 0. */
 lbm_status lbm_set_fields(lbm_handle *h, int what, const void *src, size_t bytes, int src_is_device);
+
+/* MEM re-mapping momentum charge, off by default (Algorithm 1 of the paper
+ * has no such step; the option is this library's).  The re-mapping at the
+ * end of a MEM step (Sec. 2.2) removes from the fluid the momentum
+ * sum_q c_q f_q of every cell a particle covers and creates that of every
+ * cell it uncovers (the populations rebuilt by Eq. (19)).  With enable = 1
+ * the difference dP (created minus removed) and its moment dL about the
+ * particle's new centre are kept per particle, and the next step's averaged
+ * force and torque become F - dP/dt and T - dL/dt (dt = lbm_subcycles)
+ * before the rigid-body update.  A sphere that crosses the lattice then
+ * feels the drag of the same sphere held in a uniform stream; without the
+ * charge it feels less (the finer the lattice, the smaller the gap).
+ * Switching, and lbm_set_particles, clear the pending amounts.  The charge
+ * covers cells within the refill box, which holds the new sphere while its
+ * centre moves less than 1.5 cells per axis in a step (a faster step raises
+ * LBM_ERR_UNSTABLE).  LBM_ERR_UNSUPPORTED for a PSM or uncoupled handle
+ * with enable = 1; LBM_ERR_ARG for enable other than 0 or 1. */
+lbm_status lbm_set_remap_charge(lbm_handle *h, int enable);
 
 /* Wait for all enqueued work and report device status. */
 lbm_status lbm_synchronize(lbm_handle *h);

@@ -33,7 +33,8 @@ COUPLING = {"PSM_M1B1": 0, "PSM_M2B2": 1, "PSM_M3B2": 2, "MEM_BB": 3, "MEM_CLI":
             "MEM_MR": 5, "NONE": 6}
 COLLISION = {"BGK": 0, "TRT": 1}
 STORAGE = {"f64": 0, "f32": 1, "f64ff": 2, "f64fx": 3, "f16s": 4, "bf16s": 5}
-FIELD_PDF, FIELD_PDF_PRE, FIELD_RHO, FIELD_U, FIELD_EPS, FIELD_FLAG, FIELD_PDF_F64 = range(7)
+(FIELD_PDF, FIELD_PDF_PRE, FIELD_RHO, FIELD_U, FIELD_EPS, FIELD_FLAG, FIELD_PDF_F64,
+ FIELD_REMAP_CHARGE) = range(8)
 PROFILE_CLASSES = ("bulk", "near", "force_total", "rigid_body", "refill", "other")
 
 EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_equilibrium",
@@ -47,7 +48,8 @@ EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_eq
             "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_last_error", "lbm_mlp_set_params",
             "lbm_mlp_get_params", "lbm_mlp_set_normalization", "lbm_mlp_get_normalization",
             "lbm_mlp_fit_normalization", "lbm_mlp_forward", "lbm_mlp_gradient", "lbm_mlp_train",
-            "lbm_set_force_model", "lbm_get_features", "lbm_measure_fp64_rate")
+            "lbm_set_force_model", "lbm_get_features", "lbm_measure_fp64_rate",
+            "lbm_set_remap_charge")
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS, MLP_NORM = 512, 64, 6, 37382, 1030
 BATCH_LAYOUTS = {"box32": 0, "box64": 1, "box128": 2, "plane": 3}
 
@@ -138,6 +140,7 @@ def load(build_if_missing: bool = True):
             "lbm_mlp_gradient": (i, [vp, vp, vp, i, fp, sz, dp]),
             "lbm_mlp_train": (i, [vp, vp, vp, i, i, ct.c_float, dp]),
             "lbm_set_force_model": (i, [vp, vp, ct.c_double, i]),
+            "lbm_set_remap_charge": (i, [vp, i]),
             "lbm_get_features": (i, [vp, fp, sz]),
             "lbm_measure_fp64_rate": (i, [vp, dp]),
         }
@@ -429,6 +432,10 @@ def lbm_set_force_model(h, m, u_ref: float, mode: int) -> None:
     _check(h, load().lbm_set_force_model(h, m, float(u_ref), int(mode)))
 
 
+def lbm_set_remap_charge(h, enable: int) -> None:
+    _check(h, load().lbm_set_remap_charge(h, int(enable)))
+
+
 def lbm_get_features(h, n: int) -> np.ndarray:
     a = np.empty((n, MLP_IN), dtype=np.float32)
     _check(h, load().lbm_get_features(h, _fptr(a), a.size))
@@ -538,6 +545,22 @@ class Simulation:
 
     def synchronize(self):
         lbm_synchronize(self.h)
+
+    def set_remap_charge(self, enable=True):
+        """MEM: charge the momentum of covered and uncovered cells to the
+        particle at the next step (``lbm_set_remap_charge``)."""
+        lbm_set_remap_charge(self.h, 1 if enable else 0)
+
+    def remap_charge(self) -> np.ndarray:
+        """(np, 6): the pending re-mapping charge (momentum, angular momentum)."""
+        out = np.zeros((self.np, 6))
+        lbm_get_fields(self.h, FIELD_REMAP_CHARGE, out.ctypes.data, out.nbytes, False)
+        return out
+
+    def set_remap_charge_state(self, charge: np.ndarray):
+        a = np.ascontiguousarray(charge, dtype=np.float64)
+        assert a.size == 6 * self.np
+        lbm_set_fields(self.h, FIELD_REMAP_CHARGE, a.ctypes.data, a.nbytes, False)
 
     def set_force_model(self, model, u_ref, mode=1):
         """model: an :class:`Mlp` (or None with mode 2: features only)."""

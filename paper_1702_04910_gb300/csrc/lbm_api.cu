@@ -79,6 +79,11 @@ struct lbm_handle {
     double u_ref;
     float* d_feat;     // [MAX_PARTICLES][LBM_MLP_IN]
     float* d_corr;     // [MAX_PARTICLES][LBM_MLP_OUT]
+    // re-mapping momentum charge (MEM, optional; Algorithm 1 has no such step)
+    int remap_charge;
+    double* d_charge;       // [np][6] amounts of the last re-mapping, taken off the next step
+    double* d_charge_part;  // [np][refill blocks][6] refill-block partials
+    size_t charge_part_cap; // doubles allocated in d_charge_part
     // profiling
     int profiling;
     std::vector<EventPair> events;
@@ -168,10 +173,14 @@ lbm_status free_particles(lbm_handle* h) {
     cudaFree(h->d_force);
     cudaFree(h->d_partials);
     cudaFree(h->d_map);
+    cudaFree(h->d_charge);
+    cudaFree(h->d_charge_part);
     h->d_parts = h->d_prev = h->d_tmp = nullptr;
     h->d_force = h->d_partials = nullptr;
     h->d_map = nullptr;
     h->map_cap = 0;
+    h->d_charge = h->d_charge_part = nullptr;
+    h->charge_part_cap = 0;
     if (h->h_stage) cudaFreeHost(h->h_stage);
     h->h_stage = nullptr;
     return LBM_OK;
@@ -186,6 +195,8 @@ lbm_status alloc_particles(lbm_handle* h, int n) {
     CK(h, cudaMalloc(&h->d_tmp, part_bytes), "cudaMalloc particles");
     CK(h, cudaMalloc(&h->d_force, sizeof(double) * 6 * np), "cudaMalloc forces");
     CK(h, cudaMemsetAsync(h->d_force, 0, sizeof(double) * 6 * np, h->stream), "memset");
+    CK(h, cudaMalloc(&h->d_charge, sizeof(double) * 6 * np), "cudaMalloc charge");
+    CK(h, cudaMemsetAsync(h->d_charge, 0, sizeof(double) * 6 * np, h->stream), "memset");
     CK(h, cudaMallocHost(&h->h_stage, sizeof(double) * (6 * np + 1)), "cudaMallocHost");
     h->partial_cap = 0;
     return LBM_OK;
@@ -198,6 +209,21 @@ lbm_status ensure_partials(lbm_handle* h) {
     near_grid(h->g, h->maxd, box);
     const size_t need = (size_t)h->subcycles * (size_t)near_partial_doubles(box, h->np);
     const size_t mneed0 = (size_t)map_entries(h->g, h->maxd, h->np);
+    if (h->remap_charge) {
+        // refill-block partials of the re-mapping charge (box side as in step_once)
+        const size_t cneed = (size_t)std::max(h->np, 1) * 6 *
+                             (size_t)refill_blocks((int)std::ceil(h->maxd) + 4);
+        if (cneed > h->charge_part_cap || !h->d_charge_part) {
+            if (h->d_charge_part) {
+                CK(h, cudaStreamSynchronize(h->stream), "charge partials sync");
+                cudaFree(h->d_charge_part);
+                h->d_charge_part = nullptr;
+            }
+            CK(h, cudaMalloc(&h->d_charge_part, sizeof(double) * cneed),
+               "cudaMalloc charge partials");
+            h->charge_part_cap = cneed;
+        }
+    }
     if (need <= h->partial_cap && h->d_partials && mneed0 <= h->map_cap && h->d_map) return LBM_OK;
     if (h->d_partials) {
         CK(h, cudaStreamSynchronize(h->stream), "partials sync");
@@ -284,7 +310,8 @@ lbm_status step_once(lbm_handle* h) {
     if (!coupled) return LBM_OK;
     Launch L = base_launch(h);
     int pi = prof_begin(h, PC_FINAL);
-    CK(h, launch_finalize(L, nsub, h->d_force), "force total launch");
+    CK(h, launch_finalize(L, nsub, h->d_force, h->remap_charge ? h->d_charge : nullptr),
+       "force total launch");
     prof_end(h, pi);
     if (h->model_mode) {
         // features of P^n and the flow after the sweeps; corrected force
@@ -312,8 +339,10 @@ lbm_status step_once(lbm_handle* h) {
         L.box[0] = (int)std::ceil(h->maxd) + 4;  // refill: cube side in cells
         pi = prof_begin(h, PC_REFILL);
         CK(h, launch_refill(h->storage, h->buf[1 - h->cur], h->buf[h->cur], L, h->d_prev,
-                            h->d_parts, 1),
+                            h->d_parts, 1, h->remap_charge ? h->d_charge_part : nullptr),
            "refill launch");
+        if (h->remap_charge)
+            CK(h, launch_charge_total(L, h->d_charge_part, h->d_charge), "charge total launch");
         prof_end(h, pi);
     }
     return LBM_OK;
@@ -365,7 +394,8 @@ size_t lbm_device_bytes(const lbm_handle* h) {
     if (!h) return 0;
     const size_t np = (size_t)std::max(h->np, 1);
     return h->dev_bytes + 3 * sizeof(DevParticle) * np + sizeof(double) * 6 * np +
-           sizeof(double) * h->partial_cap + sizeof(unsigned short) * h->map_cap;
+           sizeof(double) * h->partial_cap + sizeof(unsigned short) * h->map_cap +
+           sizeof(double) * 6 * np + sizeof(double) * h->charge_part_cap;
 }
 
 lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_handle** out) {
@@ -534,6 +564,9 @@ lbm_status lbm_set_particles(lbm_handle* h, int n, const lbm_particle* host_in) 
         lbm_status st = alloc_particles(h, n);
         if (st != LBM_OK) return st;
     }
+    // a replacement from the host clears the pending re-mapping charge
+    CK(h, cudaMemsetAsync(h->d_charge, 0, sizeof(double) * 6 * (size_t)std::max(n, 1), h->stream),
+       "charge reset");
     h->maxd = std::max(h->maxd, maxd);
     {
         lbm_status st = ensure_partials(h);
@@ -623,6 +656,19 @@ lbm_status lbm_get_forces(lbm_handle* h, double* F, double* T) {
     return st;
 }
 
+lbm_status lbm_set_remap_charge(lbm_handle* h, int enable) {
+    if (!h || (enable != 0 && enable != 1)) return LBM_ERR_ARG;
+    if (enable && h->kind != 2)
+        return fail(h, LBM_ERR_UNSUPPORTED, "the re-mapping momentum charge applies to MEM couplings");
+    h->remap_charge = enable;
+    if (h->d_charge)
+        CK(h, cudaMemsetAsync(h->d_charge, 0, sizeof(double) * 6 * (size_t)std::max(h->np, 1),
+                              h->stream),
+           "charge reset");
+    if (enable && h->have_particles) return ensure_partials(h);
+    return LBM_OK;
+}
+
 lbm_status lbm_get_fields(lbm_handle* h, int what, void* dst, size_t bytes, int dst_is_device) {
     if (!h || !dst) return LBM_ERR_ARG;
     const size_t n = (size_t)h->g.n;
@@ -634,9 +680,18 @@ lbm_status lbm_get_fields(lbm_handle* h, int what, void* dst, size_t bytes, int 
         case LBM_FIELD_U: need = 3 * n * sizeof(double); break;
         case LBM_FIELD_FLAG: need = n * sizeof(int); break;
         case LBM_FIELD_PDF_F64: need = (size_t)NQ * n * sizeof(double); break;
+        case LBM_FIELD_REMAP_CHARGE: need = (size_t)6 * h->np * sizeof(double); break;
         default: return fail(h, LBM_ERR_ARG, "unknown field");
     }
     if (bytes != need) return fail(h, LBM_ERR_ARG, "byte count does not match the field");
+    if (what == LBM_FIELD_REMAP_CHARGE) {
+        if (need > 0)
+            CK(h, cudaMemcpyAsync(dst, h->d_charge, need,
+                                  dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->stream),
+               "charge copy");
+        return read_status(h);
+    }
     if (what == LBM_FIELD_PDF) {
         CK(h, cudaMemcpyAsync(dst, h->buf[h->cur], need,
                               dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -663,6 +718,18 @@ lbm_status lbm_get_fields(lbm_handle* h, int what, void* dst, size_t bytes, int 
 lbm_status lbm_set_fields(lbm_handle* h, int what, const void* src, size_t bytes, int src_is_device) {
     if (!h || !src) return LBM_ERR_ARG;
     const size_t n = (size_t)h->g.n;
+    if (what == LBM_FIELD_REMAP_CHARGE) {
+        const size_t need = (size_t)6 * h->np * sizeof(double);
+        if (bytes != need) return fail(h, LBM_ERR_ARG, "byte count does not match the field");
+        if (need > 0) {
+            CK(h, cudaMemcpyAsync(h->d_charge, src, need,
+                                  src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream),
+               "charge copy");
+            CK(h, cudaStreamSynchronize(h->stream), "charge copy sync");
+        }
+        return LBM_OK;
+    }
     if (what == LBM_FIELD_PDF) {
         const size_t need = (size_t)NQ * n * h->esize;
         if (bytes != need) return fail(h, LBM_ERR_ARG, "byte count does not match the field");

@@ -900,10 +900,13 @@ __global__ void __launch_bounds__(32)
 // fixed-order force/torque total of particle q (one block per particle):
 // F = (S_1 + ... + S_nsub) / nsub with S_k the sum, over the near-kernel
 // blocks of every particle's region, of subcycle k's partials for q.
+// charge != nullptr: the pending re-mapping momentum charge of q, [q][6],
+// divided by the step's lattice time nsub, is taken off.
 __device__ __forceinline__ void finalize_block(int np, long long nblk,
                                                const double* __restrict__ partials, int nsub,
                                                double* __restrict__ out, int q,
-                                               double (*red)[6]) {
+                                               double (*red)[6],
+                                               const double* __restrict__ charge = nullptr) {
     const int tid = threadIdx.x;
     const long long count = (long long)np * nblk;
     double tot[6] = {0, 0, 0, 0, 0, 0};
@@ -929,14 +932,15 @@ __device__ __forceinline__ void finalize_block(int np, long long nblk,
         __syncthreads();
     }
     if (tid == 0)
-        for (int c = 0; c < 6; ++c) out[q * 6 + c] = tot[c] / nsub;
+        for (int c = 0; c < 6; ++c)
+            out[q * 6 + c] = charge ? tot[c] / nsub - charge[q * 6 + c] / nsub : tot[c] / nsub;
 }
 
 __global__ void __launch_bounds__(256)
     k_finalize(int np, long long nblk, const double* __restrict__ partials, int nsub,
-               double* __restrict__ out) {
+               double* __restrict__ out, const double* __restrict__ charge) {
     __shared__ double red[256][6];
-    finalize_block(np, nblk, partials, nsub, out, blockIdx.x, red);
+    finalize_block(np, nblk, partials, nsub, out, blockIdx.x, red, charge);
 }
 
 // ---------------------------------------------------------------------------
@@ -1070,13 +1074,15 @@ struct RefillWarp {
 
 // Rebuilds candidate cell (x, y, z) of particle p; all 32 lanes call it with
 // the same cell.  The pulls are spread over the lanes, the rest is computed
-// by every lane alike and lane 0 stores.
+// by every lane alike and lane 0 stores.  jm receives the momentum
+// sum_q c_q f_q of the rebuilt pre-collision populations (every lane).
 template <typename T, typename C>
 __device__ __forceinline__ void refill_warp(const T* __restrict__ srcB, T* __restrict__ dst,
                                             const Geom& g, const Coll<C>& k, const Coupl& cp,
                                             const DevParticle* so, const DevParticle* sn,
                                             int extrapolate, int p, int x, int y, int z,
-                                            int* __restrict__ status, RefillWarp& w, int lane) {
+                                            int* __restrict__ status, RefillWarp& w, int lane,
+                                            double (&jm)[3]) {
     const DevParticle& Pn = sn[p];
     const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
     double v[3];
@@ -1182,6 +1188,13 @@ __device__ __forceinline__ void refill_warp(const T* __restrict__ srcB, T* __res
         }
         equilibrium((C)rbar, (C)v[0], (C)v[1], (C)v[2], k.rho0, fn);
     }
+    jm[0] = jm[1] = jm[2] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        jm[0] += (double)fn[q] * cx(q);
+        jm[1] += (double)fn[q] * cy(q);
+        jm[2] += (double)fn[q] * cz(q);
+    }
     collide_fluid(fn, k);
     if (lane == 0) {
         if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)
@@ -1192,14 +1205,34 @@ __device__ __forceinline__ void refill_warp(const T* __restrict__ srcB, T* __res
     __syncwarp();
 }
 
+// Adds sign * (j, (x_c - X_p) x j) of cell (x, y, z) to acc, X_p the centre
+// of P (minimum image in periodic directions).
+__device__ __forceinline__ void add_cell_moment(double (&acc)[6], const Geom& g,
+                                                const DevParticle& P, int x, int y, int z,
+                                                const double (&j)[3], double sign) {
+    double r[3];
+    separation(g, x + 0.5, y + 0.5, z + 0.5, P, r[0], r[1], r[2]);
+    acc[0] += sign * j[0];
+    acc[1] += sign * j[1];
+    acc[2] += sign * j[2];
+    acc[3] += sign * (r[1] * j[2] - r[2] * j[1]);
+    acc[4] += sign * (r[2] * j[0] - r[0] * j[2]);
+    acc[5] += sign * (r[0] * j[1] - r[1] * j[0]);
+}
+
 // Candidate test of thread lid of particle p's box, then the warp's
 // candidates one after another.  Every lane of the warp must call this.
+// acc != nullptr: re-mapping momentum charge of particle p (uncovered cells
+// plus, covered cells minus; moments about the new centre) added to this
+// thread's six sums.  The box holds every cell of the new sphere while the
+// centre moves by less than 1.5 cells per axis in a step.
 template <typename T, typename C>
 __device__ __forceinline__ void refill_cells(const T* __restrict__ srcB, T* __restrict__ dst,
                                              const Geom& g, const Coll<C>& k, const Coupl& cp,
                                              const DevParticle* so, const DevParticle* sn,
                                              int extrapolate, int side, int p, long long lid,
-                                             int* __restrict__ status, RefillWarp& w, int lane) {
+                                             int* __restrict__ status, RefillWarp& w, int lane,
+                                             double (*acc)[6] = nullptr) {
     bool cand = lid < (long long)side * side * side;
     int x = 0, y = 0, z = 0;
     if (cand) {
@@ -1217,23 +1250,45 @@ __device__ __forceinline__ void refill_cells(const T* __restrict__ srcB, T* __re
             z = wrap_i(z, g.nz);
         }
     }
-    if (cand) cand = cell_owner(g, so, cp.np, x, y, z) == p + 1;
-    if (cand) cand = cell_owner(g, sn, cp.np, x, y, z) == 0;
+    const int own_old = cand ? cell_owner(g, so, cp.np, x, y, z) : -1;
+    const bool test_new = own_old == p + 1 || (acc && own_old == 0);
+    const int own_new = test_new ? cell_owner(g, sn, cp.np, x, y, z) : -1;
+    cand = own_old == p + 1 && own_new == 0;
+    if (acc && own_old == 0 && own_new == p + 1) {
+        // covered: the fluid momentum of its pre-collision populations leaves the fluid
+        C f[NQ];
+        mem_pull(srcB, g, cp, so, cp.np, (const GeoMap*)nullptr, x, y, z, lin(g, x, y, z), f,
+                 (Slots*)nullptr, status);
+        double j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            j[0] += (double)f[q] * cx(q);
+            j[1] += (double)f[q] * cy(q);
+            j[2] += (double)f[q] * cz(q);
+        }
+        add_cell_moment(*acc, g, sn[p], x, y, z, j, -1.0);
+    }
     const unsigned full = 0xffffffffu;
     for (unsigned m = __ballot_sync(full, cand); m; m &= m - 1) {
         const int src_lane = __ffs(m) - 1;
         const int cxl = __shfl_sync(full, x, src_lane), cyl = __shfl_sync(full, y, src_lane),
                   czl = __shfl_sync(full, z, src_lane);
+        double jm[3];
         refill_warp<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, p, cxl, cyl, czl, status, w,
-                          lane);
+                          lane, jm);
+        if (acc && lane == src_lane) add_cell_moment(*acc, g, sn[p], cxl, cyl, czl, jm, 1.0);
     }
 }
 
+// Grid (ceil(side^3 / REFILL_THREADS), np).  charge_part != nullptr: block
+// (bx, p) also writes its fixed-order sums of particle p's re-mapping
+// momentum charge to charge_part[(p * gridDim.x + bx) * 6 + c].
 template <typename T, typename C>
 __global__ void __launch_bounds__(REFILL_THREADS)
     k_refill(const T* __restrict__ srcB, T* __restrict__ dst, Geom g, Coll<C> k, Coupl cp,
              const DevParticle* __restrict__ p_old, const DevParticle* __restrict__ p_new,
-             int extrapolate, int side, int* __restrict__ status) {
+             int extrapolate, int side, int* __restrict__ status,
+             double* __restrict__ charge_part) {
     __shared__ DevParticle so[MAX_PARTICLES], sn[MAX_PARTICLES];
     const int tid = threadIdx.x;
     const int nd = cp.np * (int)(sizeof(DevParticle) / sizeof(double));
@@ -1243,8 +1298,45 @@ __global__ void __launch_bounds__(REFILL_THREADS)
     }
     __syncthreads();
     __shared__ RefillWarp rw[REFILL_THREADS / 32];
-    refill_cells<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, side, blockIdx.y,
-                       (long long)blockIdx.x * blockDim.x + tid, status, rw[tid >> 5], tid & 31);
+    const int p = blockIdx.y, lane = tid & 31;
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    refill_cells<T, C>(srcB, dst, g, k, cp, so, sn, extrapolate, side, p,
+                       (long long)blockIdx.x * blockDim.x + tid, status, rw[tid >> 5], lane,
+                       charge_part ? &acc : nullptr);
+    if (!charge_part) return;
+    if (tid == 0) {
+        // the box holds the new sphere only for a step of less than 1.5 cells
+        double d[3];
+        separation(g, sn[p].x[0], sn[p].x[1], sn[p].x[2], so[p], d[0], d[1], d[2]);
+        if (fabs(d[0]) >= 1.5 || fabs(d[1]) >= 1.5 || fabs(d[2]) >= 1.5)
+            atomicOr(status, ST_UNSTABLE);
+    }
+    // fixed order: a butterfly within each warp, then the warps in turn
+    __shared__ double red[REFILL_THREADS / 32][6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        double v = acc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[tid >> 5][c] = v;
+    }
+    __syncthreads();
+    if (tid < 6) {
+        double t = 0.0;
+        for (int wi = 0; wi < REFILL_THREADS / 32; ++wi) t += red[wi][tid];
+        charge_part[((long long)p * gridDim.x + blockIdx.x) * 6 + tid] = t;
+    }
+}
+
+// out[p * 6 + c] = sum over the nblk refill blocks of particle p, in order.
+__global__ void k_charge_total(int np, long long nblk, const double* __restrict__ part,
+                               double* __restrict__ out) {
+    const int t = threadIdx.x;
+    if (t >= 6 * np) return;
+    const int p = t / 6, c = t - 6 * (t / 6);
+    double s = 0.0;
+    for (long long b = 0; b < nblk; ++b) s += part[((long long)p * nblk + b) * 6 + c];
+    out[t] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1644,14 +1736,14 @@ cudaError_t near_t(const void* src, void* dst, const Launch& L) {
 
 template <typename T>
 cudaError_t refill_t(const void* srcB, void* dst, const Launch& L, const DevParticle* po,
-                     const DevParticle* pn, int extrapolate) {
+                     const DevParticle* pn, int extrapolate, double* charge_part) {
     using C = typename ComputeOf<T>::type;
     if (L.cp.np <= 0) return cudaSuccess;
     int side = L.box[0];  // set by the caller: cube side in cells
-    long long cells = (long long)side * side * side;
-    dim3 grid((unsigned)((cells + REFILL_THREADS - 1) / REFILL_THREADS), L.cp.np, 1);
+    dim3 grid((unsigned)refill_blocks(side), L.cp.np, 1);
     k_refill<T, C><<<grid, REFILL_THREADS, 0, L.stream>>>((const T*)srcB, (T*)dst, L.g, coll_of<C, C>(L),
-                                                L.cp, po, pn, extrapolate, side, L.status);
+                                                L.cp, po, pn, extrapolate, side, L.status,
+                                                charge_part);
     return cudaGetLastError();
 }
 
@@ -1715,13 +1807,21 @@ cudaError_t launch_near(int storage, const void* src, void* dst, const Launch& L
     }
 }
 cudaError_t launch_refill(int storage, const void* srcB, void* dst, const Launch& L,
-                          const DevParticle* p_old, const DevParticle* p_new, int extrapolate) {
+                          const DevParticle* p_old, const DevParticle* p_new, int extrapolate,
+                          double* charge_part) {
     switch (storage) {
-        case 1: return refill_t<float>(srcB, dst, L, p_old, p_new, extrapolate);
-        case 4: return refill_t<__half>(srcB, dst, L, p_old, p_new, extrapolate);
-        case 5: return refill_t<__nv_bfloat16>(srcB, dst, L, p_old, p_new, extrapolate);
-        default: return refill_t<double>(srcB, dst, L, p_old, p_new, extrapolate);
+        case 1: return refill_t<float>(srcB, dst, L, p_old, p_new, extrapolate, charge_part);
+        case 4: return refill_t<__half>(srcB, dst, L, p_old, p_new, extrapolate, charge_part);
+        case 5:
+            return refill_t<__nv_bfloat16>(srcB, dst, L, p_old, p_new, extrapolate, charge_part);
+        default: return refill_t<double>(srcB, dst, L, p_old, p_new, extrapolate, charge_part);
     }
+}
+cudaError_t launch_charge_total(const Launch& L, const double* charge_part, double* charge) {
+    if (L.cp.np <= 0) return cudaSuccess;
+    k_charge_total<<<1, 6 * MAX_PARTICLES, 0, L.stream>>>(L.cp.np, refill_blocks(L.box[0]),
+                                                          charge_part, charge);
+    return cudaGetLastError();
 }
 cudaError_t launch_macro(int storage, const void* state, const Launch& L, int what, void* out) {
     switch (storage) {
@@ -1772,10 +1872,10 @@ cudaError_t launch_map(const Launch& L) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out) {
+cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out, const double* charge) {
     if (L.cp.np <= 0) return cudaSuccess;
     k_finalize<<<L.cp.np, 256, 0, L.stream>>>(L.cp.np, near_blocks(L.box), L.partials, nsub,
-                                               force_out);
+                                               force_out, charge);
     return cudaGetLastError();
 }
 cudaError_t launch_rigid_body(const Launch& L, const double* force, double gx, double gy,

@@ -40,6 +40,10 @@ constexpr int NEAR_BX = 32, NEAR_BY = 2, NEAR_BZ = 1;
 constexpr int REFILL_THREADS = 128;
 static_assert(NEAR_BX * NEAR_BY * NEAR_BZ % 32 == 0, "near blocks are whole warps");
 static_assert(REFILL_THREADS % 32 == 0, "refill blocks are whole warps");
+// blocks of the refill kernel per particle for a box of side^3 cells
+inline long long refill_blocks(int side) {
+    return ((long long)side * side * side + REFILL_THREADS - 1) / REFILL_THREADS;
+}
 
 // Cells per axis of the region box that holds any particle of diameter <= maxd.
 inline void region_extent(const Geom& g, double maxd, int ext[3]) {
@@ -221,8 +225,13 @@ static_assert((int)ST_TOO_MANY_OBJECTS == (int)LBM_STATUS_TOO_MANY_OBJECTS &&
 // storage with 64-bit fixed-point collision
 cudaError_t launch_bulk(int storage, const void* src, void* dst, const Launch& L);
 cudaError_t launch_near(int storage, const void* src, void* dst, const Launch& L);
+// charge_part != nullptr: also the re-mapping momentum charge partials,
+// refill_blocks(L.box[0]) blocks x 6 doubles per particle (see k_refill)
 cudaError_t launch_refill(int storage, const void* srcB, void* dst, const Launch& L,
-                          const DevParticle* p_old, const DevParticle* p_new, int extrapolate);
+                          const DevParticle* p_old, const DevParticle* p_new, int extrapolate,
+                          double* charge_part = nullptr);
+// charge[p * 6 + c] = fixed-order total of the refill's charge partials
+cudaError_t launch_charge_total(const Launch& L, const double* charge_part, double* charge);
 cudaError_t launch_macro(int storage, const void* state, const Launch& L, int what, void* out);
 cudaError_t launch_init_eq(int storage, void* dst, const Launch& L, double rho, double ux,
                            double uy, double uz);
@@ -230,7 +239,10 @@ cudaError_t launch_from_f64(int storage, const double* in, void* dst, long long 
                             long long ncell, cudaStream_t s);
 cudaError_t launch_to_f64(int storage, const void* in, double* out, long long count,
                           long long ncell, cudaStream_t s);
-cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out);
+// charge != nullptr: the pending re-mapping momentum charge, [p][6], over nsub
+// is taken off the totals
+cudaError_t launch_finalize(const Launch& L, int nsub, double* force_out,
+                            const double* charge = nullptr);
 cudaError_t launch_regions(const Launch& L);
 // batched ensemble (all cases on one stream; see lbm_batch.cu)
 cudaError_t launch_batch_regions(BatchCase* cases, int n, cudaStream_t s);

@@ -342,6 +342,103 @@ def test_checkpoint_restart_is_bitwise(lattice, coupling):
     assert np.array_equal(b.forces()[0], ref_F[0])
 
 
+# ---- MEM re-mapping momentum charge (optional; oracle reading R32) --------------------------
+def charge_pair(case, storage="f64"):
+    from paper_1702_04910_gb300.binding import Simulation
+    kw = W.sim_kwargs(case)
+    o = Oracle(case["shape"], remap_charge=1, **kw)
+    g = Simulation(case["shape"], storage=storage, **kw)
+    g.set_remap_charge(True)
+    o.set_particles(case["particles"])
+    g.set_particles(case["particles"])
+    return o, g
+
+
+def compare_charge(o, g, tol=FORCE_TOL):
+    ref, got = o.charge(), g.remap_charge()
+    scale = np.max(np.abs(ref))
+    assert scale > 1e-6
+    err = np.max(np.abs(got - ref)) / scale
+    assert err <= tol, f"charge relative error {err:.3e} > {tol:.0e}"
+
+
+@pytest.mark.parametrize("coupling,storage", [("MEM_BB", "f64"), ("MEM_CLI", "f64"),
+                                              ("MEM_MR", "f64"), ("MEM_CLI", "f64fx")])
+def test_remap_charge_parity(lattice, coupling, storage):
+    """A free sphere crossing cells with the charge on: the pending charge
+    (covered minus uncovered cells' momentum and its moment), the forces it
+    enters, the particle state and the PDFs match the oracle at the FP64
+    bars after 25 steps."""
+    case = moving_sphere_case(coupling)
+    o, g = charge_pair(case, storage)
+    start(o, g, lattice, amp=0.02, seed=7)
+    moved = 0
+    for _ in range(25):
+        s0 = o.solid()
+        o.step(1)
+        g.step(1)
+        moved += int(((s0 > 0) != (o.solid() > 0)).sum())
+    assert moved > 0
+    compare_charge(o, g)
+    compare_pdf(o, g)
+    compare_forces(o, g)
+    compare_particles(o, g)
+    assert np.array_equal(g.flags(), o.solid())
+
+
+def test_remap_charge_two_spheres_parity(lattice):
+    """Each cell's amount goes to the particle that covers or uncovers it."""
+    case = moving_sphere_case("MEM_CLI", shape=(48, 40, 40))
+    p0 = dict(case["particles"][0])
+    p0["x"] = (14.3, 20.1, 20.4)
+    p1 = dict(p0)
+    p1["x"] = (31.6, 19.2, 21.3)
+    p1["u"] = (-0.03, 0.05, 0.02)
+    case["particles"] = [p0, p1]
+    o, g = charge_pair(case)
+    start(o, g, lattice, amp=0.02, seed=2)
+    o.step(15)
+    g.step(15)
+    assert np.all(np.abs(o.charge()).max(axis=1) > 1e-6)
+    compare_charge(o, g)
+    compare_forces(o, g)
+    compare_particles(o, g)
+
+
+def test_remap_charge_off_by_default_and_checkpointed(lattice):
+    """Off: the pending charge stays zero and the step is unchanged.  On: a
+    restart from the PDFs, the particles and the pending charge continues
+    bit for bit; switching on a PSM handle is refused."""
+    from paper_1702_04910_gb300.binding import LbmError, Simulation
+    case = moving_sphere_case("MEM_BB")
+    kw = W.sim_kwargs(case)
+    plain = Simulation(case["shape"], **kw)
+    plain.set_particles(case["particles"])
+    plain.init_equilibrium()
+    plain.step(4)
+    assert not np.any(plain.remap_charge())
+    a = Simulation(case["shape"], **kw)
+    a.set_remap_charge(True)
+    a.set_particles(case["particles"])
+    a.init_equilibrium()
+    a.step(4)
+    saved = a.pdf(), a.get_particles(), a.remap_charge()
+    assert np.any(saved[2])
+    a.step(4)
+    ref_f, ref_F = a.pdf(), a.forces()
+    b = Simulation(case["shape"], **kw)
+    b.set_remap_charge(True)
+    b.set_particles(saved[1])
+    b.set_pdf(saved[0])
+    b.set_remap_charge_state(saved[2])
+    b.step(4)
+    assert np.array_equal(b.pdf(), ref_f)
+    assert np.array_equal(b.forces()[0], ref_F[0]) and np.array_equal(b.forces()[1], ref_F[1])
+    psm = Simulation(case["shape"], **W.sim_kwargs(moving_sphere_case("PSM_M2B2")))
+    with pytest.raises(LbmError):
+        psm.set_remap_charge(True)
+
+
 # ---- FP32 storage and arithmetic ------------------------------------------------------------
 @pytest.mark.parametrize("coupling", ["PSM_M2B2", "MEM_CLI", "MEM_MR"])
 def test_fp32_storage_tracks_fp64(lattice, coupling):
