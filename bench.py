@@ -180,12 +180,17 @@ def run_ensemble(args, stream, world, dist, barrier, peak, storages=("f64", "f64
 
     cases = W.ensemble(args.ensemble_cases, seed=0)
     cells = sum(int(np.prod(c["shape"])) for c in cases)
-    near = sum(near_cells(c["particles"][0], c["shape"]) for c in cases)
+    # near-particle cell updates per step (MEM cases sweep twice, PSM once)
+    near_updates = sum(near_cells(c["particles"][0], c["shape"]) * sweeps_of(c["coupling"])
+                       for c in cases)
     out = {}
     for storage in storages:
         b = Batch(cases, storage=storage, stream=stream)
         layouts, grid, tune_ms = b.autotune(reps=3)
+        b.profile(True)  # bulk sweeps timed on the device inside the timed steps
         b.step(args.warmup)
+        b.synchronize()
+        b.profile(True)  # clears the counter: only the timed steps count
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
@@ -194,9 +199,15 @@ def run_ensemble(args, stream, world, dist, barrier, peak, storages=("f64", "f64
         barrier()
         ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
         b.synchronize()  # raises if a case reported a device status
+        bulk_ms_sum, bulk_sweeps = b.profile_read()
         parts = b.particles()
         cu = b.cell_updates
-        bulk_gbps = 2 * 19 * 8 * (cells - near) / (tune_ms * 1e-3) / 1e9
+        # bulk sweeps: every cell update away from the particles, 304 B each,
+        # over the device time of the bulk sweeps of a timed step
+        bulk_ms = bulk_ms_sum / max(bulk_sweeps, 1)
+        sweeps_per_step = bulk_sweeps / max(args.steps, 1)
+        bulk_step_ms = bulk_ms_sum / max(args.steps, 1)
+        bulk_gbps = 2 * 19 * 8 * (cu - near_updates) / (bulk_step_ms * 1e-3) / 1e9
         out[f"ensemble{len(cases)}_{storage}"] = {
             "value": world * cu * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
             "ms_per_step": ms / args.steps, "steps": args.steps, "cases": len(cases),
@@ -204,7 +215,11 @@ def run_ensemble(args, stream, world, dist, barrier, peak, storages=("f64", "f64
             "workload": "seeded ensemble: D ~ U{8..20}, domain round(5.3D)^2 x round(16D), "
                         "Ga ~ U(100, 250), density ratio 1.5, PSM M1B1/M2B2 and MEM BB/CLI/MR",
             "tuning": {"layouts": {k: layouts.count(k) for k in sorted(set(layouts))},
-                       "grid_blocks": grid, "bulk_ms": tune_ms},
+                       "grid_blocks": grid, "bulk_ms_when_tuned": tune_ms},
+            "bulk_avg_launch_ms": bulk_ms, "bulk_sweeps_per_step": sweeps_per_step,
+            "bulk_ms_per_step": bulk_step_ms, "bulk_cell_updates_per_step": cu - near_updates,
+            "bulk_timing": "device global-timer stamps around every bulk sweep of the "
+                           "timed steps (lbm_batch_profile_enable)",
             "bulk_GBps": bulk_gbps, "frac": bulk_gbps / peak,
             "graph_kernels_per_step": b.graph_kernels,
             "gpu_launches": b.graph_kernels * args.steps,

@@ -408,6 +408,17 @@ lbm_status lbm_batch_get_pdf(lbm_batch *b, int c, double *host_out, size_t bytes
  * count each sweep). */
 long long lbm_batch_cell_updates(const lbm_batch *b);
 
+/* Device timing of the batch's bulk sweeps (a measurement aid; the paper has
+ * no counterpart).  enable = 1 rebuilds the step graph with a one-thread
+ * stamp kernel before and after every bulk-sweep launch (two more kernels
+ * per LBM sweep, counted by lbm_batch_graph_kernels); they read the GPU's
+ * nanosecond global timer and add each bulk sweep's span to a device
+ * counter.  Enabling, or disabling, clears the counter.
+ * lbm_batch_profile_read returns the summed milliseconds and the number of
+ * bulk sweeps timed since then; it synchronises the stream. */
+lbm_status lbm_batch_profile_enable(lbm_batch *b, int enable);
+lbm_status lbm_batch_profile_read(lbm_batch *b, double *bulk_ms, long long *launches);
+
 /* Device bytes held by the batch. */
 size_t lbm_batch_device_bytes(const lbm_batch *b);
 

@@ -49,7 +49,7 @@ EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_eq
             "lbm_mlp_get_params", "lbm_mlp_set_normalization", "lbm_mlp_get_normalization",
             "lbm_mlp_fit_normalization", "lbm_mlp_forward", "lbm_mlp_gradient", "lbm_mlp_train",
             "lbm_set_force_model", "lbm_get_features", "lbm_measure_fp64_rate",
-            "lbm_set_remap_charge")
+            "lbm_set_remap_charge", "lbm_batch_profile_enable", "lbm_batch_profile_read")
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS, MLP_NORM = 512, 64, 6, 37382, 1030
 BATCH_LAYOUTS = {"box32": 0, "box64": 1, "box128": 2, "plane": 3}
 
@@ -125,6 +125,8 @@ def load(build_if_missing: bool = True):
             "lbm_batch_cell_updates": (ct.c_longlong, [vp]),
             "lbm_batch_device_bytes": (sz, [vp]),
             "lbm_batch_graph_kernels": (i, [vp]),
+            "lbm_batch_profile_enable": (i, [vp, i]),
+            "lbm_batch_profile_read": (i, [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]),
             "lbm_batch_synchronize": (i, [vp]),
             "lbm_batch_destroy": (None, [vp]),
             "lbm_batch_last_error": (ct.c_char_p, [vp]),
@@ -352,6 +354,16 @@ def lbm_batch_graph_kernels(b) -> int:
 
 def lbm_batch_synchronize(b) -> None:
     _bcheck(b, load().lbm_batch_synchronize(b))
+
+
+def lbm_batch_profile_enable(b, enable: int) -> None:
+    _bcheck(b, load().lbm_batch_profile_enable(b, int(enable)))
+
+
+def lbm_batch_profile_read(b):
+    ms, n = ct.c_double(), ct.c_longlong()
+    _bcheck(b, load().lbm_batch_profile_read(b, ct.byref(ms), ct.byref(n)))
+    return ms.value, n.value
 
 
 def lbm_batch_destroy(b) -> None:
@@ -633,6 +645,14 @@ class Batch:
 
     def synchronize(self):
         lbm_batch_synchronize(self.b)
+
+    def profile(self, enable=True):
+        """Time every bulk sweep on the device from now on (graph rebuilt)."""
+        lbm_batch_profile_enable(self.b, 1 if enable else 0)
+
+    def profile_read(self):
+        """(summed bulk-sweep milliseconds, bulk sweeps timed)."""
+        return lbm_batch_profile_read(self.b)
 
 
 class Mlp:

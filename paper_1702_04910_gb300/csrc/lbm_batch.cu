@@ -79,6 +79,8 @@ struct lbm_batch {
     cudaGraphExec_t exec;
     int graph_kernels;
     long long cell_updates;
+    int profiling;                 // the graph brackets each bulk sweep with stamps
+    unsigned long long* dprof;     // [start, summed ns, launches]
     char err[512];
 };
 
@@ -202,7 +204,15 @@ cudaError_t enqueue_step(lbm_batch* b, int* kernels) {
         }
         if (e == cudaSuccess) e = launch_batch_near(b->dcases, nl.view(), nl.total, sub, b->dstatus, b->side);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
+        if (e == cudaSuccess && b->profiling) {
+            e = launch_stamp(b->dprof, 0, s);
+            ++k;
+        }
         if (e == cudaSuccess) e = launch_batch_bulk(b->mode, b->dcases, bl.view(), bl.total, b->grid, b->dstatus, s);
+        if (e == cudaSuccess && b->profiling) {
+            e = launch_stamp(b->dprof, 1, s);
+            ++k;
+        }
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
         if (e == cudaSuccess) e = launch_batch_swap(b->dcases, nl.view(), s);
         k += 3;
@@ -371,6 +381,7 @@ void release(lbm_batch* b) {
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
+    if (b->dprof) cudaFree(b->dprof);
     if (b->arena) cudaFree(b->arena);
     delete b;
 }
@@ -697,6 +708,31 @@ long long lbm_batch_cell_updates(const lbm_batch* b) { return b ? b->cell_update
 size_t lbm_batch_device_bytes(const lbm_batch* b) { return b ? b->arena_bytes : 0; }
 
 int lbm_batch_graph_kernels(const lbm_batch* b) { return b ? b->graph_kernels : 0; }
+
+lbm_status lbm_batch_profile_enable(lbm_batch* b, int enable) {
+    if (!b || (enable != 0 && enable != 1)) return LBM_ERR_ARG;
+    if (enable && !b->dprof)
+        BK(b, cudaMalloc(&b->dprof, 3 * sizeof(unsigned long long)), "cudaMalloc profile");
+    if (b->dprof)
+        BK(b, cudaMemsetAsync(b->dprof, 0, 3 * sizeof(unsigned long long), b->stream),
+           "profile reset");
+    if (enable == b->profiling) return LBM_OK;
+    b->profiling = enable;
+    return build_graph(b);
+}
+
+lbm_status lbm_batch_profile_read(lbm_batch* b, double* bulk_ms, long long* launches) {
+    if (!b || !bulk_ms || !launches) return LBM_ERR_ARG;
+    unsigned long long h[3] = {0, 0, 0};
+    if (b->dprof) {
+        BK(b, cudaMemcpyAsync(h, b->dprof, sizeof(h), cudaMemcpyDeviceToHost, b->stream),
+           "profile copy");
+        BK(b, cudaStreamSynchronize(b->stream), "profile sync");
+    }
+    *bulk_ms = (double)h[1] * 1e-6;
+    *launches = (long long)h[2];
+    return read_status(b);
+}
 
 lbm_status lbm_batch_synchronize(lbm_batch* b) {
     if (!b) return LBM_ERR_ARG;

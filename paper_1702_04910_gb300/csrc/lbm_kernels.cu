@@ -1935,6 +1935,24 @@ cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_
     k_batch_rigid<<<(n + 63) / 64, 64, 0, s>>>(cases, n, status);
     return cudaGetLastError();
 }
+// Device time stamp (the GPU's nanosecond global timer): end = 0 keeps it in
+// p[0]; end = 1 adds the span since p[0] to p[1] and counts it in p[2].  One
+// thread; launched on the stream of the work it brackets.
+__global__ void k_stamp(unsigned long long* p, int end) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (!end) {
+        p[0] = t;
+    } else {
+        p[1] += t - p[0];
+        p[2] += 1;
+    }
+}
+cudaError_t launch_stamp(unsigned long long* p, int end, cudaStream_t s) {
+    k_stamp<<<1, 1, 0, s>>>(p, end);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, int* status,
                                 cudaStream_t s) {
     if (l.n == 0 || total == 0) return cudaSuccess;

@@ -255,6 +255,9 @@ cudaError_t launch_batch_bulk(int mode, BatchCase* cases, BatchList l, long long
 cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s);
 cudaError_t launch_batch_finalize(BatchCase* cases, int n, cudaStream_t s);
 cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_t s);
+// p[0] = now (end = 0); p[1] += now - p[0], p[2] += 1 (end = 1); now from
+// the global nanosecond timer
+cudaError_t launch_stamp(unsigned long long* p, int end, cudaStream_t s);
 cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, int* status,
                                 cudaStream_t s);
 cudaError_t launch_batch_init(BatchCase* cases, int n, long long max_cells, cudaStream_t s);

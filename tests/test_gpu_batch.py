@@ -154,3 +154,39 @@ def test_batch_single_case_equals_handle_path_forces():
     g.close()
     for k in ("x", "u"):
         assert np.linalg.norm(pb[k] - pg[k]) <= 1e-11 * max(np.linalg.norm(pg[k]), 1e-3)
+
+
+def test_batch_bulk_profile_counts_every_sweep_and_changes_nothing():
+    """lbm_batch_profile_enable brackets every bulk sweep of the step graph
+    with two stamp kernels: the counter sees one span per LBM sweep (MEM
+    cases make two sweeps per step), the graph grows by two kernels per
+    sweep, the spans are positive and below the wall time of the steps, and
+    the simulation state stays bit for bit that of an unprofiled batch."""
+    import time
+
+    from paper_1702_04910_gb300.binding import Batch
+    cases = small_ensemble(seed=5)
+    plain = Batch(cases)
+    k0 = plain.graph_kernels
+    plain.step(4)
+    ref = batch_state(plain)
+    plain.close()
+    b = Batch(cases)
+    b.profile(True)
+    sweeps = (b.graph_kernels - k0) // 2
+    assert sweeps == 2 and b.graph_kernels == k0 + 4
+    b.synchronize()
+    t0 = time.perf_counter()
+    b.step(4)
+    b.synchronize()
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    ms, n = b.profile_read()
+    assert n == 4 * sweeps
+    assert 0.0 < ms < wall_ms
+    got = batch_state(b)
+    b.profile(False)
+    assert b.graph_kernels == k0 and b.profile_read() == (0.0, 0)
+    b.close()
+    for c in range(len(cases)):
+        assert np.array_equal(got[0][c], ref[0][c]), c
+    assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
