@@ -632,10 +632,16 @@ struct PullPair<T, NQ> {
 };
 
 // Grid (ceil(nx / (2 PAIR_TX)), ceil(ny / PAIR_TY), nz), block (PAIR_TX, PAIR_TY).
-constexpr int PAIR_TX = 64, PAIR_TY = 4;
+// One row of 128 cells per 64-thread block: the near-particle sweep runs
+// beside this kernel and each of its blocks holds 7.7k (MEM) to 11.5k (PSM)
+// registers; with small bulk blocks an SM that hosts near blocks gives up
+// only as many bulk warps as their registers need (measured in the 128 x 128
+// x 512 step, FP16: 0.70 of HBM with 64 x 4, 0.745 with 64 x 2, 0.76 with
+// 64 x 1; 32 x 1 and 128 x 1 are slower).
+constexpr int PAIR_TX = 64, PAIR_TY = 1;
 
 template <typename T>
-__global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 3)
+__global__ void __launch_bounds__(PAIR_TX * PAIR_TY, 768 / (PAIR_TX * PAIR_TY))
     k_bulk_pair(const T* __restrict__ src, T* __restrict__ dst, Geom g, Coll<float> k,
                 const DevParticle* __restrict__ parts, int np, int* __restrict__ status) {
     const int bx0 = 2 * blockIdx.x * PAIR_TX, by0 = blockIdx.y * PAIR_TY;

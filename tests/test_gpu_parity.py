@@ -384,6 +384,7 @@ def test_remap_charge_parity(lattice, coupling, storage):
     compare_forces(o, g)
     compare_particles(o, g)
     assert np.array_equal(g.flags(), o.solid())
+    g.close()
 
 
 def test_remap_charge_two_spheres_parity(lattice):
@@ -403,6 +404,7 @@ def test_remap_charge_two_spheres_parity(lattice):
     compare_charge(o, g)
     compare_forces(o, g)
     compare_particles(o, g)
+    g.close()
 
 
 def test_remap_charge_off_by_default_and_checkpointed(lattice):
@@ -417,6 +419,7 @@ def test_remap_charge_off_by_default_and_checkpointed(lattice):
     plain.init_equilibrium()
     plain.step(4)
     assert not np.any(plain.remap_charge())
+    plain.close()
     a = Simulation(case["shape"], **kw)
     a.set_remap_charge(True)
     a.set_particles(case["particles"])
@@ -434,9 +437,14 @@ def test_remap_charge_off_by_default_and_checkpointed(lattice):
     b.step(4)
     assert np.array_equal(b.pdf(), ref_f)
     assert np.array_equal(b.forces()[0], ref_F[0]) and np.array_equal(b.forces()[1], ref_F[1])
+    a.close()
+    b.close()
     psm = Simulation(case["shape"], **W.sim_kwargs(moving_sphere_case("PSM_M2B2")))
-    with pytest.raises(LbmError):
-        psm.set_remap_charge(True)
+    try:
+        with pytest.raises(LbmError):
+            psm.set_remap_charge(True)
+    finally:
+        psm.close()
 
 
 # ---- FP32 storage and arithmetic ------------------------------------------------------------

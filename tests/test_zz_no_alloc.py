@@ -10,6 +10,8 @@ handle, within the parity tolerances used elsewhere (PDFs 1e-12 relative,
 forces 1e-10 relative), leave the device's free memory unchanged, and raise
 no status bit.  This file is named to be collected last.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -60,6 +62,9 @@ def test_noalloc_sweep_matches_handle_step(lattice, coupling):
     bufs = [torch.from_numpy(state0).cuda(), torch.empty_like(torch.from_numpy(state0)).cuda()]
     ft = torch.zeros(6, dtype=torch.float64, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    # objects of earlier tests that only the cycle collector frees would
+    # otherwise release device memory between the readings below
+    gc.collect()
     torch.cuda.synchronize()
     free = []
     for call, (ref, F, T) in enumerate(((ref1, F1, T1), (ref2, F2, T2))):
