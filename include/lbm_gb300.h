@@ -408,6 +408,12 @@ lbm_status lbm_batch_get_pdf(lbm_batch *b, int c, double *host_out, size_t bytes
  * count each sweep). */
 long long lbm_batch_cell_updates(const lbm_batch *b);
 
+/* The re-mapping momentum charge of lbm_set_remap_charge (off by default),
+ * switched for every MEM case of the batch (PSM cases have no re-mapping and
+ * are unaffected).  Clears the pending amounts and rebuilds the step graph
+ * (one more kernel per step when on); synchronises. */
+lbm_status lbm_batch_set_remap_charge(lbm_batch *b, int enable);
+
 /* Device timing of the batch's bulk sweeps (a measurement aid; the paper has
  * no counterpart).  enable = 1 rebuilds the step graph with a one-thread
  * stamp kernel before and after every bulk-sweep launch (two more kernels

@@ -49,7 +49,8 @@ EXPORTED = ("lbm_create", "lbm_set_particles", "lbm_get_particles", "lbm_init_eq
             "lbm_mlp_get_params", "lbm_mlp_set_normalization", "lbm_mlp_get_normalization",
             "lbm_mlp_fit_normalization", "lbm_mlp_forward", "lbm_mlp_gradient", "lbm_mlp_train",
             "lbm_set_force_model", "lbm_get_features", "lbm_measure_fp64_rate",
-            "lbm_set_remap_charge", "lbm_batch_profile_enable", "lbm_batch_profile_read")
+            "lbm_set_remap_charge", "lbm_batch_profile_enable", "lbm_batch_profile_read",
+            "lbm_batch_set_remap_charge")
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS, MLP_NORM = 512, 64, 6, 37382, 1030
 BATCH_LAYOUTS = {"box32": 0, "box64": 1, "box128": 2, "plane": 3}
 
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = True):
             "lbm_batch_device_bytes": (sz, [vp]),
             "lbm_batch_graph_kernels": (i, [vp]),
             "lbm_batch_profile_enable": (i, [vp, i]),
+            "lbm_batch_set_remap_charge": (i, [vp, i]),
             "lbm_batch_profile_read": (i, [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]),
             "lbm_batch_synchronize": (i, [vp]),
             "lbm_batch_destroy": (None, [vp]),
@@ -354,6 +356,10 @@ def lbm_batch_graph_kernels(b) -> int:
 
 def lbm_batch_synchronize(b) -> None:
     _bcheck(b, load().lbm_batch_synchronize(b))
+
+
+def lbm_batch_set_remap_charge(b, enable: int) -> None:
+    _bcheck(b, load().lbm_batch_set_remap_charge(b, int(enable)))
 
 
 def lbm_batch_profile_enable(b, enable: int) -> None:
@@ -645,6 +651,10 @@ class Batch:
 
     def synchronize(self):
         lbm_batch_synchronize(self.b)
+
+    def set_remap_charge(self, enable=True):
+        """MEM cases: charge the re-mapping momentum (``lbm_batch_set_remap_charge``)."""
+        lbm_batch_set_remap_charge(self.b, 1 if enable else 0)
 
     def profile(self, enable=True):
         """Time every bulk sweep on the device from now on (graph rebuilt)."""

@@ -80,6 +80,7 @@ struct lbm_batch {
     int graph_kernels;
     long long cell_updates;
     int profiling;                 // the graph brackets each bulk sweep with stamps
+    int any_charge;                // a MEM case charges its re-mapping momentum
     unsigned long long* dprof;     // [start, summed ns, launches]
     char err[512];
 };
@@ -223,6 +224,10 @@ cudaError_t enqueue_step(lbm_batch* b, int* kernels) {
     if (e == cudaSuccess && b->refill_l.n > 0) {
         e = launch_batch_refill(b->dcases, b->refill_l.view(), b->refill_l.total, b->dstatus, s);
         ++k;
+        if (e == cudaSuccess && b->any_charge) {
+            e = launch_batch_charge_total(b->dcases, b->n, s);
+            ++k;
+        }
     }
     *kernels = k;
     return e;
@@ -503,7 +508,8 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
         list_off(b->near_l[s], nl[s], nb[s]);
         list_off(b->bulk_l[s], bl[s], bb[s]);
     }
-    std::vector<size_t> o_buf0(n_cases), o_buf1(n_cases), o_part(n_cases), o_map(n_cases);
+    std::vector<size_t> o_buf0(n_cases), o_buf1(n_cases), o_part(n_cases), o_map(n_cases),
+        o_chg(n_cases), o_cpart(n_cases);
     for (int c = 0; c < n_cases; ++c) {
         const BatchCase& k = b->hc[c];
         const size_t pdf = sizeof(double) * (size_t)NQ * (size_t)k.g.n;
@@ -511,6 +517,8 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
         o_buf1[c] = take(pdf);
         o_part[c] = take(sizeof(double) * 6 * (size_t)k.subcycles * (size_t)k.nblk);
         o_map[c] = take(sizeof(unsigned short) * (size_t)k.map_ext[0] * k.map_ext[1] * k.map_ext[2]);
+        o_chg[c] = take(sizeof(double) * 6);
+        o_cpart[c] = take(sizeof(double) * 6 * (size_t)refill_blocks(k.refill_side));
     }
     b->arena_bytes = off;
 
@@ -553,6 +561,9 @@ lbm_status lbm_batch_create(int n_cases, const lbm_config* cfgs, const lbm_parti
         k.buf[1] = (double*)(base + o_buf1[c]);
         k.partials = (double*)(base + o_part[c]);
         k.map = (unsigned short*)(base + o_map[c]);
+        k.charge = (double*)(base + o_chg[c]);
+        k.charge_part = (double*)(base + o_cpart[c]);
+        k.remap_charge = 0;
         k.part = b->dparts + c;
         k.prev = b->dprev + c;
         k.force = b->dforce + 6 * c;
@@ -708,6 +719,25 @@ long long lbm_batch_cell_updates(const lbm_batch* b) { return b ? b->cell_update
 size_t lbm_batch_device_bytes(const lbm_batch* b) { return b ? b->arena_bytes : 0; }
 
 int lbm_batch_graph_kernels(const lbm_batch* b) { return b ? b->graph_kernels : 0; }
+
+lbm_status lbm_batch_set_remap_charge(lbm_batch* b, int enable) {
+    if (!b || (enable != 0 && enable != 1)) return LBM_ERR_ARG;
+    BK(b, cudaStreamSynchronize(b->stream), "charge sync");
+    int any = 0;
+    for (int i = 0; i < b->n; ++i) {
+        BatchCase& c = b->hc[i];
+        c.remap_charge = c.kind == 2 ? enable : 0;
+        any |= c.remap_charge;
+        // cur lives on the device and is flipped there: write only this field
+        BK(b, cudaMemcpyAsync(&b->dcases[i].remap_charge, &c.remap_charge, sizeof(int),
+                              cudaMemcpyHostToDevice, b->stream),
+           "case upload");
+        BK(b, cudaMemsetAsync(c.charge, 0, sizeof(double) * 6, b->stream), "charge reset");
+    }
+    BK(b, cudaStreamSynchronize(b->stream), "charge sync");  // host records above
+    b->any_charge = any;
+    return build_graph(b);
+}
 
 lbm_status lbm_batch_profile_enable(lbm_batch* b, int enable) {
     if (!b || (enable != 0 && enable != 1)) return LBM_ERR_ARG;

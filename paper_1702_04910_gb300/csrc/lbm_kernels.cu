@@ -1286,6 +1286,36 @@ __device__ __forceinline__ void refill_cells(const T* __restrict__ srcB, T* __re
     }
 }
 
+// The refill box holds the new sphere only for a step of less than 1.5
+// cells per axis: a faster step is reported as unstable.
+__device__ __forceinline__ void charge_step_check(const Geom& g, const DevParticle& Pn,
+                                                  const DevParticle& Po, int* status) {
+    double d[3];
+    separation(g, Pn.x[0], Pn.x[1], Pn.x[2], Po, d[0], d[1], d[2]);
+    if (fabs(d[0]) >= 1.5 || fabs(d[1]) >= 1.5 || fabs(d[2]) >= 1.5) atomicOr(status, ST_UNSTABLE);
+}
+
+// Fixed-order sum of the block's per-thread charge sums into out[0..6): a
+// butterfly within each warp, then the warps in turn.  Every thread of the
+// REFILL_THREADS-thread block calls it.
+__device__ __forceinline__ void charge_block_sum(const double (&acc)[6], double* out) {
+    __shared__ double red[REFILL_THREADS / 32][6];
+    const int tid = threadIdx.x, lane = tid & 31;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        double v = acc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[tid >> 5][c] = v;
+    }
+    __syncthreads();
+    if (tid < 6) {
+        double t = 0.0;
+        for (int wi = 0; wi < REFILL_THREADS / 32; ++wi) t += red[wi][tid];
+        out[tid] = t;
+    }
+}
+
 // Grid (ceil(side^3 / REFILL_THREADS), np).  charge_part != nullptr: block
 // (bx, p) also writes its fixed-order sums of particle p's re-mapping
 // momentum charge to charge_part[(p * gridDim.x + bx) * 6 + c].
@@ -1310,28 +1340,8 @@ __global__ void __launch_bounds__(REFILL_THREADS)
                        (long long)blockIdx.x * blockDim.x + tid, status, rw[tid >> 5], lane,
                        charge_part ? &acc : nullptr);
     if (!charge_part) return;
-    if (tid == 0) {
-        // the box holds the new sphere only for a step of less than 1.5 cells
-        double d[3];
-        separation(g, sn[p].x[0], sn[p].x[1], sn[p].x[2], so[p], d[0], d[1], d[2]);
-        if (fabs(d[0]) >= 1.5 || fabs(d[1]) >= 1.5 || fabs(d[2]) >= 1.5)
-            atomicOr(status, ST_UNSTABLE);
-    }
-    // fixed order: a butterfly within each warp, then the warps in turn
-    __shared__ double red[REFILL_THREADS / 32][6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        double v = acc[c];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) red[tid >> 5][c] = v;
-    }
-    __syncthreads();
-    if (tid < 6) {
-        double t = 0.0;
-        for (int wi = 0; wi < REFILL_THREADS / 32; ++wi) t += red[wi][tid];
-        charge_part[((long long)p * gridDim.x + blockIdx.x) * 6 + tid] = t;
-    }
+    if (tid == 0) charge_step_check(g, sn[p], so[p], status);
+    charge_block_sum(acc, charge_part + ((long long)p * gridDim.x + blockIdx.x) * 6);
 }
 
 // out[p * 6 + c] = sum over the nblk refill blocks of particle p, in order.
@@ -1628,7 +1638,8 @@ __global__ void __launch_bounds__(256) k_batch_finalize(BatchCase* __restrict__ 
     __shared__ double red[256][6];
     const BatchCase& B = cases[blockIdx.x];
     const int nsub = B.kind != 0 ? B.subcycles : 1;
-    finalize_block(1, B.nblk, B.partials, nsub, B.force, 0, red);
+    finalize_block(1, B.nblk, B.partials, nsub, B.force, 0, red,
+                   B.remap_charge ? B.charge : nullptr);
 }
 
 __global__ void k_batch_rigid(BatchCase* __restrict__ cases, int n, int* __restrict__ status) {
@@ -1655,9 +1666,29 @@ __global__ void __launch_bounds__(REFILL_THREADS)
     __syncthreads();
     const int cur = B.cur;
     __shared__ RefillWarp rw[REFILL_THREADS / 32];
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     refill_cells<double, double>(B.buf[1 - cur], B.buf[cur], B.g, B.kd, B.cp, so, sn, 1,
                                  B.refill_side, 0, local * blockDim.x + threadIdx.x, status,
-                                 rw[threadIdx.x >> 5], threadIdx.x & 31);
+                                 rw[threadIdx.x >> 5], threadIdx.x & 31,
+                                 B.remap_charge ? &acc : nullptr);
+    // re-mapping charge: block partial `local` of this case (see k_refill)
+    if (!B.remap_charge) return;
+    if (threadIdx.x == 0) charge_step_check(B.g, sn[0], so[0], status);
+    charge_block_sum(acc, B.charge_part + local * 6);
+}
+
+// Per case with the charge on: charge[c] = the fixed-order total of its
+// refill-block partials.  One thread per (case, component).
+__global__ void k_batch_charge_total(BatchCase* __restrict__ cases, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 6 * n) return;
+    const BatchCase& B = cases[t / 6];
+    if (!B.remap_charge) return;
+    const int c = t % 6;
+    const long long nb = refill_blocks(B.refill_side);
+    double s = 0.0;
+    for (long long k = 0; k < nb; ++k) s += B.charge_part[k * 6 + c];
+    B.charge[c] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1935,6 +1966,10 @@ cudaError_t launch_batch_swap(BatchCase* cases, BatchList l, cudaStream_t s) {
 }
 cudaError_t launch_batch_finalize(BatchCase* cases, int n, cudaStream_t s) {
     k_batch_finalize<<<n, 256, 0, s>>>(cases);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_charge_total(BatchCase* cases, int n, cudaStream_t s) {
+    k_batch_charge_total<<<(6 * n + 255) / 256, 256, 0, s>>>(cases, n);
     return cudaGetLastError();
 }
 cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_t s) {

@@ -41,7 +41,7 @@ constexpr int REFILL_THREADS = 128;
 static_assert(NEAR_BX * NEAR_BY * NEAR_BZ % 32 == 0, "near blocks are whole warps");
 static_assert(REFILL_THREADS % 32 == 0, "refill blocks are whole warps");
 // blocks of the refill kernel per particle for a box of side^3 cells
-inline long long refill_blocks(int side) {
+__host__ __device__ inline long long refill_blocks(int side) {
     return ((long long)side * side * side + REFILL_THREADS - 1) / REFILL_THREADS;
 }
 
@@ -100,6 +100,9 @@ struct BatchCase {
     long long nblk;
     int refill_side;
     double gravity[3];
+    int remap_charge;     // MEM: charge the re-mapping momentum (lbm_batch_set_remap_charge)
+    double* charge;       // 6 doubles: pending amounts of the last re-mapping
+    double* charge_part;  // refill_blocks(refill_side) x 6 block partials
 };
 
 // Work list of a batched launch: cases list[0..n) with prefix sums base[] of
@@ -258,6 +261,8 @@ cudaError_t launch_batch_rigid(BatchCase* cases, int n, int* status, cudaStream_
 // p[0] = now (end = 0); p[1] += now - p[0], p[2] += 1 (end = 1); now from
 // the global nanosecond timer
 cudaError_t launch_stamp(unsigned long long* p, int end, cudaStream_t s);
+// per case with the charge on: total of its refill-block charge partials
+cudaError_t launch_batch_charge_total(BatchCase* cases, int n, cudaStream_t s);
 cudaError_t launch_batch_refill(BatchCase* cases, BatchList l, long long total, int* status,
                                 cudaStream_t s);
 cudaError_t launch_batch_init(BatchCase* cases, int n, long long max_cells, cudaStream_t s);

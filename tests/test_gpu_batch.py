@@ -190,3 +190,35 @@ def test_batch_bulk_profile_counts_every_sweep_and_changes_nothing():
     for c in range(len(cases)):
         assert np.array_equal(got[0][c], ref[0][c]), c
     assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+
+
+def test_batch_remap_charge_matches_oracle_per_case():
+    """The re-mapping momentum charge (oracle reading R32) switched on for a
+    batch: every MEM case, given a velocity so that it crosses cells, matches
+    its oracle run with the charge on (PSM cases, unaffected, with theirs);
+    the step graph gains the one charge-total kernel."""
+    from paper_1702_04910_gb300.binding import Batch
+    cases = small_ensemble(seed=9)
+    for case in cases:
+        if case["coupling"] in MEM:
+            case["particles"][0]["u"] = (0.04, -0.03, -0.05)
+    steps = 20
+    b = Batch(cases)
+    k0 = b.graph_kernels
+    b.set_remap_charge(True)
+    assert b.graph_kernels == k0 + 1
+    b.step(steps)
+    pdfs, F, T, parts = batch_state(b)
+    b.close()
+    charged = 0
+    for c, case in enumerate(cases):
+        mem = case["coupling"] in MEM
+        o = Oracle(case["shape"], remap_charge=1 if mem else 0, **W.sim_kwargs(case))
+        o.init_equilibrium(case["rho0"], (0.0, 0.0, 0.0))
+        o.set_particles(case["particles"])
+        o.step(steps)
+        if mem:
+            charged += int(np.abs(o.charge()).max() > 1e-6)
+        check_case(o, case, pdfs[c], F[c], T[c], parts[c])
+        o.close()
+    assert charged == 3
