@@ -12,7 +12,14 @@
 //   k_finalize  fixed-order sum of the block partials, subcycle average;
 //   k_rigid     explicit Euler rigid-body update;
 //   k_refill    MEM re-mapping: PDF reconstruction Eq. (19) of uncovered
-//               cells, then their collision.
+//               cells, then their collision; optionally the momentum the
+//               covered and uncovered cells exchange with the fluid, as
+//               fixed-order block partials (k_charge_total adds them, and
+//               the next k_finalize takes them off the force);
+//   k_bulk_pair the 16-bit bulk sweep, two x-neighbours per thread in packed
+//               f32x2 arithmetic.
+// The batched ensemble has k_batch_* counterparts of these; k_stamp reads
+// the global timer around a launch for device-side timing.
 #include <cuda_runtime.h>
 
 #include <type_traits>
