@@ -696,7 +696,11 @@ def run_ours(args):
             "data": "synthetic (seeded workload, no dataset)",
             "config": {"workload": WORKLOAD if args.scale == 1.0 else f"{WORKLOAD} (scaled by {args.scale})",
                        "shape": list(shape), "couplings": list(args.couplings),
-                       "lbm_sweeps_per_step": sweeps_per_step, "collision": "TRT (Lambda=3/16)",
+                       "lbm_sweeps_per_step": sweeps_per_step,
+                       # the same rate counted per global step (one step of each coupling,
+                       # MEM's two sweeps counted once): value x couplings / sweeps
+                       "mlups_per_global_step": value * len(args.couplings) / sweeps_per_step,
+                       "collision": "TRT (Lambda=3/16)",
                        "precision": "FP64 PDFs and collision; FP64 forces and rigid-body update",
                        "l2": "inputs larger than L2 (2.55 GB of PDFs per simulation)",
                        "replicas_per_rank": 1},
