@@ -387,6 +387,30 @@ def test_remap_charge_parity(lattice, coupling, storage):
     g.close()
 
 
+# Reduced precision: the charge sums the momentum of a few dozen cells from
+# the stored (rounded) populations, so it carries their relative error times
+# the cancellation between covered and uncovered cells (a few times the PDF
+# bar); measured on GB300: FP32 ~1e-5, FP16 ~5e-4, BF16 ~2e-3 (bars >= 10x).
+@pytest.mark.parametrize("coupling,storage,pdf_tol,force_tol,charge_tol",
+                         [("MEM_CLI", "f32", 1e-5, 1e-3, 1e-4),
+                          ("MEM_MR", "f32", 1e-5, 1e-3, 1e-4),
+                          ("MEM_CLI", "f16s", 2e-4, 1e-2, 5e-3),
+                          ("MEM_BB", "f16s", 2e-4, 1e-2, 5e-3),
+                          ("MEM_CLI", "bf16s", 2e-3, 5e-2, 2e-2)])
+def test_remap_charge_tracks_fp64_in_reduced_precision(lattice, coupling, storage, pdf_tol,
+                                                       force_tol, charge_tol):
+    case = moving_sphere_case(coupling)
+    o, g = charge_pair(case, storage)
+    start(o, g, lattice)
+    o.step(25)
+    g.step(25)
+    compare_charge(o, g, tol=charge_tol)
+    compare_pdf(o, g, tol=pdf_tol)
+    compare_forces(o, g, tol=force_tol)
+    assert np.array_equal(g.flags(), o.solid())
+    g.close()
+
+
 def test_remap_charge_two_spheres_parity(lattice):
     """Each cell's amount goes to the particle that covers or uncovers it."""
     case = moving_sphere_case("MEM_CLI", shape=(48, 40, 40))
