@@ -71,6 +71,16 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     lib.lbm_step.restype = ct.c_int
     lib.lbm_step.argtypes = [ct.c_void_p, ct.c_int]
     assert lib.lbm_step(None, 1) == binding.LBM_ERR_ARG
+    # the re-mapping charge and the batch's bulk timing check their handle first
+    for name in ("lbm_set_remap_charge", "lbm_batch_set_remap_charge", "lbm_batch_profile_enable"):
+        fn = getattr(lib, name)
+        fn.restype = ct.c_int
+        fn.argtypes = [ct.c_void_p, ct.c_int]
+        assert fn(None, 1) == binding.LBM_ERR_ARG, name
+    lib.lbm_batch_profile_read.restype = ct.c_int
+    lib.lbm_batch_profile_read.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    ms, n = ct.c_double(), ct.c_longlong()
+    assert lib.lbm_batch_profile_read(None, ct.byref(ms), ct.byref(n)) == binding.LBM_ERR_ARG
 
 
 def test_struct_layouts_match_header():
@@ -97,20 +107,24 @@ def test_enum_values_match_header():
         assert re.search(rf"{name}\s*=\s*{st}\b", text), name
     for name, bit in binding.STATUS_BITS.items():
         assert re.search(rf"{name}\s*=\s*{bit}\b", text), name
+    for name in ("PDF", "PDF_PRE", "RHO", "U", "EPS", "FLAG", "PDF_F64", "REMAP_CHARGE"):
+        val = getattr(binding, f"FIELD_{name}")
+        assert re.search(rf"LBM_FIELD_{name}\s*=\s*{val}\b", text), name
 
 
 def test_binding_wrapper_surface():
     """The Python wrapper keeps the methods the tests and the benchmark use."""
     for name in ("set_particles", "get_particles", "init_equilibrium", "step", "forces",
                  "set_pdf_pre", "pdf", "pdf_f64", "set_pdf", "macro", "eps", "flags",
-                 "synchronize", "close"):
+                 "synchronize", "close", "set_remap_charge", "remap_charge",
+                 "set_remap_charge_state"):
         assert callable(getattr(binding.Simulation, name)), name
     for name in binding.EXPORTED:
         if name not in ("lbm_last_error", "lbm_abi_version", "lbm_batch_last_error",
                         "lbm_mlp_last_error"):
             assert callable(getattr(binding, name)), name
     for name in ("step", "autotune", "set_tuning", "particles", "forces", "pdf", "synchronize",
-                 "close"):
+                 "close", "set_remap_charge", "profile", "profile_read"):
         assert callable(getattr(binding.Batch, name)), name
 
 
