@@ -266,11 +266,16 @@ def test_psm_momentum_balance(lattice, coupling, subcycles, collision):
     _, j0 = moments(f0, c)
     o.step(1)
     F, _ = o.forces()
-    _, j1 = moments(o.pdf("pre"), c)
+    f1 = o.pdf("pre")
+    _, j1 = moments(f1, c)
     dJ = j1.reshape(3, -1).sum(axis=1) - j0.reshape(3, -1).sum(axis=1)
     expect = subcycles * (fext * (1.0 - B).sum() - F[0])
     assert np.allclose(dJ, expect, atol=1e-13)
     assert np.max(np.abs(F)) > 1e-4  # the exchange is not trivially zero
+    # mass: every solid operator M1-M3 and the forcing have zero population
+    # sum (the incompressible f_eq sums to rho at any velocity), so the box's
+    # mass is unchanged
+    assert abs(f1.sum() - f0.sum()) < 1e-12 * f0.sum()
 
 
 @pytest.mark.parametrize("coupling", ["PSM_M1B1", "PSM_M2B2", "PSM_M3B2"])
