@@ -510,6 +510,33 @@ def test_shifted_16bit_storage_tracks_fp64(lattice, coupling, storage, pdf_tol, 
     compare_forces(o, g, tol=force_tol)
 
 
+# ---- wall contact (reading R13) -------------------------------------------------------------
+@pytest.mark.parametrize("coupling", ["PSM_M2B2", "MEM_BB", "MEM_CLI"])
+def test_wall_contact_parity(lattice, coupling):
+    """A sphere driven into the closed floor, held one cell off it: the
+    particle state, forces and PDFs match the oracle at the FP64 bars through
+    the contact (the near region runs against the wall)."""
+    case = moving_sphere_case(coupling, D=8.0, shape=(24, 24, 32))
+    case["wall_contact"] = 1
+    p = case["particles"][0]
+    p["x"] = (12.2, 11.9, 4.0 + 1.5)
+    p["u"] = (0.01, 0.0, -0.12)
+    p["omega"] = (0.0, 0.0, 0.0)
+    p["fixed"] = 0
+    o, g = make_pair(case)
+    start(o, g, lattice, amp=0.01, seed=3)
+    held = 0
+    for _ in range(12):
+        o.step(1)
+        g.step(1)
+        held += int(abs(o.get_particles()[0]["x"][2] - 5.0) < 1e-12)
+    assert held >= 3
+    compare_particles(o, g)
+    compare_forces(o, g)
+    compare_pdf(o, g)
+    g.close()
+
+
 # ---- failure reporting ---------------------------------------------------------------------
 def test_particle_leaving_through_a_wall_is_reported():
     from paper_1702_04910_gb300.binding import LbmError, Simulation, LBM_ERR_DOMAIN

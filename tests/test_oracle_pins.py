@@ -975,3 +975,37 @@ def test_remap_charge_restores_galilean_drag(coupling):
     assert plain < 0.93
     assert abs(charged - 1.0) < 0.1
     assert abs(charged - 1.0) < abs(plain - 1.0)
+
+
+@pytest.mark.parametrize("coupling", ["PSM_M2B2", "MEM_CLI"])
+def test_wall_contact_keeps_the_sphere_one_cell_off_the_floor(coupling):
+    """Reading R13 (wall contact on closed z walls): a sphere driven into the
+    floor never brings its surface closer than one cell; a step that would
+    take it closer puts it back at one cell and zeroes its velocity towards
+    the wall.  With the explicit Euler update (position with the old
+    velocity) a held sphere therefore alternates between zero and a small
+    wall-ward velocity that gravity and the flow give it in one step: it
+    never builds up, and the sphere does not rebound."""
+    D, R = 8.0, 4.0
+    o = Oracle((24, 24, 32), coupling=coupling, tau=0.8, bc_z=1, wall_contact=1,
+               gravity=(0.0, 0.0, -2e-4))
+    o.set_particles([{"x": (12.2, 11.9, R + 1.5), "u": (0.01, 0.0, -0.12), "diameter": D,
+                      "density": 1.5}])
+    o.init_equilibrium()
+    gaps, uz = [], []
+    for _ in range(15):
+        assert o.step(1) == 0
+        p = o.get_particles()[0]
+        gaps.append(p["x"][2] - R)
+        uz.append(p["u"][2])
+        assert np.all(np.isfinite(p["u"])) and np.all(np.isfinite(o.forces()[0]))
+    gaps, uz = np.array(gaps), np.array(uz)
+    assert np.all(gaps >= 1.0 - 1e-12)
+    held = np.abs(gaps - 1.0) < 1e-12
+    assert held.sum() >= 3
+    for k in range(len(held) - 1):
+        if held[k] and held[k + 1]:
+            assert max(uz[k], uz[k + 1]) >= 0.0  # zeroed at least every other step
+    first = int(np.argmax(held))
+    assert np.all(uz[first:] < 1e-3)                # no rebound
+    assert np.all(np.abs(uz[first:]) < 0.25 * 0.12)  # no build-up towards the wall
