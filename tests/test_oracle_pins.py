@@ -214,7 +214,8 @@ def test_mem_mapping_is_cell_centres_in_ball():
 
 # ---- exact invariants of the coupling -----------------------------------------------------
 @pytest.mark.parametrize("coupling", ALL_COUPLED)
-def test_uniform_translation_is_force_free(lattice, coupling):
+@pytest.mark.parametrize("rho", [1.0, 1.2])
+def test_uniform_translation_is_force_free(lattice, coupling, rho):
     """Galilean invariance (Sec. 2.2 force with the boundary velocity
     subtracted, Sec. 2.3 solid operators): a sphere moving with the uniform
     fluid velocity V leaves f = f_eq(rho0, V) unchanged and feels no force.
@@ -223,14 +224,17 @@ def test_uniform_translation_is_force_free(lattice, coupling):
     -v (f~_q - f_qbar) acts at x_b = x + delta_q c_q, and the discrete chord
     sums differ between lattice directions, so a small torque V x (...) remains
     (an exact property of Eq. (16)-(18) with CLI, not round-off).  For MR the
-    check holds only with alpha = 2 (kappa_1 + kappa_0 + kappa_-1)."""
+    check holds only with alpha = 2 (kappa_1 + kappa_0 + kappa_-1).  At a
+    fluid density rho != rho0 the check also fixes the density in the
+    moving-wall term of Eq. (12)-(15) to rho0, as printed: the incompressible
+    equilibrium carries momentum rho0 V whatever rho is."""
     c, w, _ = lattice
     V = np.array([0.03, -0.02, 0.015])
     shape = (20, 20, 20)
     o = Oracle(shape, coupling=coupling, collision="TRT", tau=0.8)
     o.set_particles([{"x": (9.7, 10.2, 10.45), "u": V, "diameter": 8.4, "fixed": 1}])
-    o.init_equilibrium(1.0, V)
-    feq = np.array([orc.feq(q, 1.0, V) for q in range(19)])
+    o.init_equilibrium(rho, V)
+    feq = np.array([orc.feq(q, rho, V) for q in range(19)])
     for _ in range(3):
         o.step(1)
         F, T = o.forces()
